@@ -1,0 +1,86 @@
+"""Pins for the oracle's global RBF and RBF-PU interpolation (Sec. 2.1, 2.3, 3.3).
+
+Global: the interpolant reproduces the data at the nodes (Eq. rbf_linsys), the evaluation
+equals numpy's dense product, smooth fields are reproduced between the nodes.
+PU: closed-form values of the weight functions (Eq. bspline, Wendland C2), partition of
+unity (constants reproduced), interpolation at the nodes, exact reproduction of spherical
+harmonics of degree <= ell (each patch interpolant reproduces them, Eq. rbf_poly).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.special import sph_harm_y
+
+from paper_1804_01609_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_global_interpolates_at_nodes_and_between(orc):
+    X = inputs.nodes(642, 1)
+    G = orc.GlobalInterpolator(X, orc.GAUSS, 6.0)
+    f = inputs.gaussian_hills(X, [[0.6, 0.8, 0.0]], 5.0, 0.95)
+    C = G.coefficients(f)
+    A = np.exp(-36.0 * ((X[:, None] - X[None]) ** 2).sum(-1))
+    np.testing.assert_allclose(A @ C, f, atol=1e-12)           # s|_X = f|_X
+    np.testing.assert_allclose(orc.global_eval(X, X, C, orc.GAUSS, 6.0), A @ C, atol=1e-13)
+    np.testing.assert_allclose(C, np.linalg.solve(A, f), rtol=1e-6, atol=1e-9)
+    P = inputs.random_unit_vectors(200, np.random.default_rng(2))
+    s = G.apply(P, f)
+    exact = inputs.gaussian_hills(P, [[0.6, 0.8, 0.0]], 5.0, 0.95)
+    assert np.abs(s - exact).max() < 5e-4  # a smooth field is well resolved at N = 642
+
+
+def test_global_imq_kernel_matches_definition(orc):
+    for r in (0.0, 0.3, 1.7):
+        assert orc.kernel(orc.IMQ, 2.5, r) == pytest.approx((1 + (2.5 * r) ** 2) ** -0.5, rel=1e-15)
+        assert orc.kernel(orc.GAUSS, 6.0, r) == pytest.approx(math.exp(-(6.0 * r) ** 2), rel=1e-14)
+        assert orc.kernel(orc.PHS, 5.0, r) == pytest.approx(r ** 5, rel=1e-14, abs=1e-300)
+
+
+def test_pu_weight_functions_closed_form(orc):
+    """Values fixed by Eq. bspline and the Wendland C2 function (tests/golden/pu_weights.txt)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "pu_weights.txt")) if l.strip() and not l.startswith("#")]
+    for kind, r, v in rows:
+        k = orc.BSPLINE if kind == "bspline" else orc.WENDLAND
+        assert orc.pu_phi(k, float(r)) == pytest.approx(float(v), rel=1e-14, abs=1e-15)
+    # continuity of the B-spline at r = 1/2 and its support
+    e = 1e-9
+    assert abs(orc.pu_phi(orc.BSPLINE, 0.5 - e) - orc.pu_phi(orc.BSPLINE, 0.5 + e)) < 1e-8
+    assert orc.pu_phi(orc.BSPLINE, 1.0) == 0.0 and orc.pu_phi(orc.WENDLAND, 1.0) == 0.0
+
+
+def _pu(orc, N=2562, n=60, ell=3, power=7, wkind=0):
+    X = inputs.nodes(N, 4)
+    Mp = math.ceil(2.5 * N / n)              # Eq. num_patches with a = 2.5
+    Om = inputs.fibonacci_nodes(Mp)
+    return X, orc.PUInterpolator(X, Om, n, ell, power, weight_kind=wkind)
+
+
+@pytest.mark.parametrize("wkind", [0, 1])
+def test_pu_partition_of_unity_and_node_interpolation(orc, wkind):
+    X, pu = _pu(orc, wkind=wkind)
+    P = inputs.random_unit_vectors(300, np.random.default_rng(5))
+    one = pu.apply(P, np.ones(len(X)))
+    np.testing.assert_allclose(one, 1.0, atol=1e-12)
+    f = inputs.cosine_bell(X, [0, 0, 1], 0.8)
+    np.testing.assert_allclose(pu.apply(X, f), f, atol=1e-10)
+
+
+def test_pu_reproduces_spherical_harmonics(orc):
+    X, pu = _pu(orc)
+    P = inputs.random_unit_vectors(200, np.random.default_rng(6))
+    for (l, m) in [(1, 0), (2, 1), (3, -2), (3, 3)]:
+        def f(Q):
+            th = np.arccos(np.clip(Q[:, 2], -1, 1)); ph = np.arctan2(Q[:, 1], Q[:, 0])
+            Y = sph_harm_y(l, abs(m), th, ph)
+            return Y.real if m >= 0 else Y.imag
+        np.testing.assert_allclose(pu.apply(P, f(X)), f(P), atol=1e-10)
+
+
+def test_pu_every_point_covered(orc):
+    X, pu = _pu(orc)
+    P = inputs.random_unit_vectors(2000, np.random.default_rng(7))
+    assert np.isfinite(pu.apply(P, np.ones(len(X)))).all()
