@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark: node-updates/s of the local RBF-SL step on one GB300 (mixed and FP64).
+
+Workload (one "step" = one SL step of Algorithm 1: RK4 departure points, k-NN stencils,
+FP64 saddle-point weights, gather-dot W.q over all tracers): N = 40,962 Fibonacci nodes
+(1e-3 rad jitter), stencils of n = 84 nearest nodes of each departure point, PHS r^5,
+spherical harmonics to degree 4, reversing deformational flow psi = 2.4 y^2 cos(pi t) over
+600 steps (T_f = 1), 33 tracers (two Gaussian hills + 31 smooth random fields). Mixed
+precision = FP64 solves, FP32 tracing displacement and FP32 difference-form W.q.
+
+The L2 cache (129 MB) is flushed between timed steps by writing a 256 MB buffer, so every
+step starts cold. Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-updates/s per SL step, mixed vs FP64 at equal l2 err; p50/p99 solve latency"
+UNIT = "node-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--accuracy-steps", type=int, default=600,
+                    help="steps of the full-trajectory accuracy runs (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_1804_01609_gb300 import inputs
+    return inputs.config_local_deformation()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 ALU peak of a GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+# (NVIDIA's 1.25 TFLOP/s FP64 figure for the part; the clock is the maximum SM clock).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def weights_flops(m):
+    """Algorithmic FP64 flops of one augmented solve: LU of an m x m system with one
+    right-hand side ((2/3) m^3 for the elimination, 2 m^2 for the rhs and back substitution)."""
+    return 2.0 / 3.0 * m ** 3 + 2.0 * m ** 2
+
+
+def make_ctx(w, precision, stream, rbfsl):
+    ctx = rbfsl.Context(0, stream=stream)
+    ctx.set_nodes(w.X)
+    ctx.set_velocity(w.vel_kind, w.vel_params)
+    ctx.set_method(rbfsl.LOCAL, rbfsl.DIRECT)
+    ctx.set_stencil_size(w.n)
+    ctx.set_sh_degree(w.ell)
+    ctx.set_kernel(rbfsl.PHS, w.power)
+    ctx.set_precision(precision)
+    ctx.set_dt(w.dt)
+    ctx.set_time(0.0)
+    q0 = w.q0()
+    ctx.set_tracers(q0.astype(np.float32) if precision == rbfsl.MIXED else q0)
+    return ctx
+
+
+def timed_steps(ctx, K, W, stream, flush, torch):
+    for _ in range(W):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ctx.step(1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in ev])
+
+
+def time_op(fn, K, stream, flush, torch):
+    fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        ev[i][0].record(stream)
+        fn()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def accuracy_run(w, precision, steps, stream, rbfsl):
+    ctx = make_ctx(w, precision, stream, rbfsl)
+    ctx.step(steps)
+    q = ctx.get_q(dtype=np.float64)
+    st = ctx.get_stats()
+    ctx.close()
+    return q, st
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def cpu_baseline(w, budget_s=10.0):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded sample: departure
+    points of one step for all nodes, then brute-force k-NN + GEPP weights + gather for the
+    first S nodes, with S sized to ~budget_s of work."""
+    import oracle
+    oracle.build()
+    X = w.X
+    q = w.q0()
+    Xi = oracle.trace_rk4(X, w.vel_kind, w.vel_params, w.dt, w.dt)
+    S = 256
+    t0 = time.perf_counter()
+    oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
+    dt0 = time.perf_counter() - t0
+    S = int(min(w.N, max(256, S * budget_s / max(dt0, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
+    el = time.perf_counter() - t0
+    return {"value": S / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{S} of {w.N} node-updates of one SL step (brute-force k-NN, GEPP, "
+                      f"gather of {w.T} tracers; FP64 C + OpenMP); {el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = workload()
+    import oracle
+    oracle.build()
+    X, q = w.X, w.q0()
+    Xi = oracle.trace_rk4(X, w.vel_kind, w.vel_params, w.dt, w.dt)
+    S = 512  # node-updates per reference step: a bounded sample of the workload's step
+    for _ in range(args.warmup):
+        oracle.local_apply(X, Xi[:64], q, w.n, w.ell, oracle.PHS, float(w.power))
+    times = []
+    for k in range(args.steps):
+        rows = np.arange(k * S, (k + 1) * S) % w.N
+        t0 = time.perf_counter()
+        oracle.trace_rk4(X[rows], w.vel_kind, w.vel_params, w.dt, w.dt)
+        oracle.local_apply(X, Xi[rows], q, w.n, w.ell, oracle.PHS, float(w.power))
+        times.append(time.perf_counter() - t0)
+    el = float(np.sum(times))
+    v = S * args.steps / el
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^5 T=33 (sampled)",
+                   "sample_nodes_per_step": S},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{S} node-updates per step of the workload, FP64 oracle"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1804_01609_gb300 import rbfsl
+    rbfsl.load()
+    w = workload()
+    N, n, T = w.N, w.n, w.T
+    m = n + (w.ell + 1) ** 2
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: mixed precision (headline), then FP64
+    ctx = make_ctx(w, rbfsl.MIXED, stream, rbfsl)
+    barrier()
+    with ClockSampler(local) as clk:
+        step_ms = timed_steps(ctx, args.steps, args.warmup, stream, flush, torch)
+    barrier()
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * N * args.steps / total_s
+
+    # dominant kernel (FP64 stencil solve) and the gather-dot, timed alone on the same stream
+    xi_t, I_t, _ = ctx.last_step_tensors(n, torch.float32)
+    x_t = torch.as_tensor(w.X, device="cuda")
+    w32 = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    rbfsl.rbfsl_stencil_weights(x_t, I_t, n, w.ell, rbfsl.PHS, w.power, xi_t, w32, stream=stream)
+    w_ms = time_op(lambda: rbfsl.rbfsl_stencil_weights(x_t, I_t, n, w.ell, rbfsl.PHS, w.power,
+                                                       xi_t, w32, stream=stream),
+                   max(3, min(args.steps, 10)), stream, flush, torch)
+    q32 = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
+    qo = torch.empty_like(q32)
+    g_ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I_t, w32, q32, qo, stream=stream), 10, stream,
+                   flush, torch)
+    ctx.close()
+
+    ctx64 = make_ctx(w, rbfsl.FP64, stream, rbfsl)
+    step64_ms = timed_steps(ctx64, max(3, min(args.steps, 10)), 1, stream, flush, torch)
+    ctx64.close()
+    value64 = N / (float(step64_ms.mean()) / 1e3)
+
+    # ---- end to end through the public API with host buffers (pinned), per step:
+    # H2D of the field, one SL step, D2H of the new field
+    ctx = make_ctx(w, rbfsl.MIXED, stream, rbfsl)
+    hq = torch.from_numpy(w.q0().astype(np.float32)).pin_memory()
+    ctx.step(1)
+    torch.cuda.synchronize()
+    K2 = args.steps
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        ctx.set_tracers(hq)
+        ctx.step(1)
+        ctx.get_q(out=hq)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    ctx.close()
+    e2e = {"value": world * N * K2 / e2e_s if world == 1 else N * K2 / e2e_s * world,
+           "unit": UNIT, "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": N * T * 4}
+
+    # ---- accuracy of full trajectories (outside the timed region)
+    acc = {}
+    if args.accuracy_steps > 0:
+        S = min(args.accuracy_steps, w.steps)
+        q0 = w.q0()
+        q64, st64 = accuracy_run(w, rbfsl.FP64, S, stream, rbfsl)
+        qmx, stmx = accuracy_run(w, rbfsl.MIXED, S, stream, rbfsl)
+        acc = {"steps": S, "t_final": S * w.dt}
+        if S == w.steps:  # the flow reverses: exact solution at T_f is the initial field
+            acc.update({"fp64_l2_vs_exact": rel_l2(q64, q0), "fp64_linf_vs_exact": rel_linf(q64, q0),
+                        "mixed_l2_vs_exact": rel_l2(qmx, q0), "mixed_linf_vs_exact": rel_linf(qmx, q0)})
+            acc["mixed_within_1pct_of_fp64"] = bool(
+                abs(acc["mixed_l2_vs_exact"] - acc["fp64_l2_vs_exact"]) <= 0.01 * acc["fp64_l2_vs_exact"])
+        acc["mixed_l2_vs_fp64"] = rel_l2(qmx, q64)
+        acc["singular_points"] = int(st64.singular_points + stmx.singular_points)
+        acc["knn_failures"] = int(st64.knn_failures + stmx.knn_failures)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    pk = peaks()
+    w_flops = N * weights_flops(m)
+    w_tflops = w_flops / (w_ms * 1e-3) / 1e12
+    g_bytes = N * n * (4 + 4) + N * T * 4 * 2
+    g_gbs = g_bytes / (g_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve + f32 trace/gather",
+        "data": "synthetic",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^5 T=33 (direct stencils)",
+                   "N": N, "n": n, "ell": w.ell, "phs_power": w.power, "tracers": T,
+                   "precision": "mixed", "l2": "flushed between timed steps (256 MB write)"},
+        "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                            "p99": float(np.percentile(step_ms, 99))},
+        "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
+        "accuracy": acc,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "weights_direct_kernel (FP64 GEPP)",
+                     "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
+                     "ms_per_launch": w_ms},
+        "roofline_gather": {"bound": "hbm", "kernel": "gather_dot_kernel<float>",
+                            "achieved": g_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                            "frac": g_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                            "traffic": None, "ms_per_launch": g_ms,
+                            "note": "W and q fit in L2 at this N; see the N=655362 W.q measurement"},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

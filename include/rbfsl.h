@@ -1,0 +1,192 @@
+/*
+ * rbfsl.h -- C ABI of the GB300 library for RBF semi-Lagrangian (SL) transport on the unit
+ * sphere (Shankar & Wright, "Mesh-free semi-Lagrangian methods for transport on a sphere
+ * using radial basis functions").
+ *
+ * Two layers:
+ *  1. A context that follows the paper's problem statement (Algorithm 1, "Input"): a
+ *     velocity field tangent to S^2, an initial field q(x, 0), the node set X, a time step
+ *     and a number of steps. rbfsl_step() runs whole SL steps on the device.
+ *  2. Stateless per-step operations on caller-owned device buffers (departure points,
+ *     k-nearest-neighbour stencils, stencil weights, the gather-dot W.q). The context calls
+ *     the same kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: RBFSL_OK (0) or a negative RBFSL_E* code; no call aborts the process.
+ *  - Layouts are row-major C arrays: points are N x 3 (x, y, z) doubles; tracer fields are
+ *    N x T (tracer index fastest); stencils are Nq x n int32 node indices (0-based).
+ *  - Device pointers must be allocated on the device current for the call (or the context's
+ *    device); `stream` is a cudaStream_t (NULL = the legacy default stream). Stateless
+ *    operations are asynchronous with respect to the host: they validate their arguments,
+ *    enqueue kernels and return. Per-point failures are reported in the optional device
+ *    array `status` (0 = ok, else an RBFSL_E* code) once the stream has reached them.
+ *  - The library never keeps a caller pointer after a call returns.
+ */
+#ifndef RBFSL_H
+#define RBFSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+enum {
+    RBFSL_OK = 0,
+    RBFSL_EINVAL = -1,     /* a size, kind or pointer argument is invalid */
+    RBFSL_ENOTCONF = -2,   /* a required setter has not been called */
+    RBFSL_ENOMEM = -3,     /* device allocation failed */
+    RBFSL_ESINGULAR = -4,  /* a stencil / patch / global system met a zero pivot */
+    RBFSL_EUNCOVERED = -5, /* a point lies in no RBF-PU patch */
+    RBFSL_ETIMEDOUT = -6,  /* a bounded device-side wait gave up */
+    RBFSL_ECUDA = -7,      /* a CUDA runtime call failed (see rbfsl_last_error) */
+    RBFSL_EKNN = -8        /* the neighbour search could not bracket k neighbours */
+};
+
+/* Velocity fields (the ODE of Sec. 3.2, Eq. sl_ode, is integrated in Cartesian form).
+ * RBFSL_VEL_RIGID:     u = omega (a x x); params = {a_x, a_y, a_z, omega}, |a| = 1
+ *                      (solid-body rotation, Sec. 4.1, for any axis).
+ * RBFSL_VEL_DEFORM_Y2: u = x cross grad(psi), psi = kappa y^2 cos(pi t / T_f);
+ *                      params = {kappa, T_f}. Reverses at t = T_f / 2 and returns every
+ *                      parcel at t = T_f (a reversing deformational flow, Sec. 4.2). */
+enum { RBFSL_VEL_RIGID = 0, RBFSL_VEL_DEFORM_Y2 = 1 };
+
+/* Interpolation method (Sec. 3.3). */
+enum { RBFSL_LOCAL = 0, RBFSL_GLOBAL = 1, RBFSL_PU = 2 };
+
+/* Local stencil choice. RBFSL_DIRECT: the n nearest nodes of each departure point, with a
+ * fresh saddle-point solve per point and step. RBFSL_CENTER: the stencil of the departure
+ * point's nearest node (that node and its n-1 nearest neighbours, Sec. 2.2 and 3.3). */
+enum { RBFSL_DIRECT = 0, RBFSL_CENTER = 1 };
+
+/* Radial kernels (Sec. 2.4): RBFSL_PHS r^p with odd p (param = p); RBFSL_GAUSS
+ * exp(-(eps r)^2) and RBFSL_IMQ (1 + (eps r)^2)^(-1/2) (param = eps). */
+enum { RBFSL_PHS = 0, RBFSL_GAUSS = 1, RBFSL_IMQ = 2 };
+
+/* Precision. RBFSL_FP64: every step in FP64. RBFSL_MIXED: saddle-point solves in FP64;
+ * departure tracing as an FP32 displacement added to the FP64 node; weights stored and
+ * the gather-dot evaluated in FP32 in difference form q_c + sum_j w_j (q_j - q_c). */
+enum { RBFSL_FP64 = 0, RBFSL_MIXED = 1 };
+
+enum { RBFSL_F64 = 0, RBFSL_F32 = 1 };    /* element types of caller buffers */
+enum { RBFSL_HOST = 0, RBFSL_DEVICE = 1 }; /* where a caller buffer lives */
+
+/* Limits of this build. */
+#define RBFSL_MAX_SH_DEGREE 8     /* ell <= 8, (ell+1)^2 <= 81 harmonics */
+#define RBFSL_MAX_SYSTEM 160      /* n + (ell+1)^2 <= 160 for one saddle-point system */
+#define RBFSL_MAX_K 256           /* neighbours per k-NN query */
+
+/* ================================================================== stateless operations */
+
+/* Departure points (Sec. 3.2, Eq. sl_ode): for each node x_j, integrate d xi/dt = u(xi, t)
+ * backward from (x_j, t1) to t1 - dt with classical RK4 (h = -dt), projecting every stage
+ * point and the result orthogonally onto S^2.
+ *   x, xi: device, N x 3 doubles (may not alias). vel_params: HOST array (4 or 2 doubles).
+ *   precision RBFSL_FP64 traces in FP64; RBFSL_MIXED evaluates the stages in FP32 and adds
+ *   the FP32 displacement to the FP64 node before the final FP64 projection.
+ * Errors: EINVAL (N < 0, null pointers, unknown kind or precision), ECUDA. */
+int rbfsl_trace_rk4(const double *x, int64_t N, int vel_kind, const double *vel_params,
+                    double t1, double dt, int precision, double *xi, void *stream);
+
+/* Spatial index for k-nearest-neighbour queries over a fixed node set (replaces the
+ * kd-tree of Sec. 3.3): a uniform grid over [-1,1]^3 whose cells hold the nodes sorted by
+ * cell. The index owns copies of the nodes (device memory, freed by _destroy).
+ *   x: device, N x 3 doubles. k_hint: the typical k of later queries (sets the cell size).
+ * Creation synchronises `stream`. Errors: EINVAL, ENOMEM, ECUDA. */
+typedef struct rbfsl_knn_index rbfsl_knn_index;
+int rbfsl_knn_index_create(rbfsl_knn_index **out, const double *x, int64_t N, int k_hint,
+                           void *stream);
+int rbfsl_knn_index_destroy(rbfsl_knn_index *index);
+
+/* The k nearest nodes of each query point, ascending by the key (d2, node index) with
+ * d2 = ((qx-x)^2 + (qy-y)^2) + (qz-z)^2, every operation rounded to nearest in FP64 (no
+ * fused multiply-add): the result equals a brute-force search, ties to the smaller index.
+ *   q: device, Nq x 3 doubles. idx: device, Nq x k int32. status: device Nq int32 or NULL
+ *   (RBFSL_EKNN where the search failed; idx row then -1).
+ * Errors: EINVAL (k < 1, k > RBFSL_MAX_K, k > N), ECUDA. */
+int rbfsl_knn_query(const rbfsl_knn_index *index, const double *q, int64_t Nq, int k,
+                    int32_t *idx, int32_t *status, void *stream);
+
+/* Stencil weights of the augmented local RBF interpolant (Sec. 2.2, Eqs. rbf_poly and
+ * rbf_poly_linsys). For point p_i with stencil S = idx[i, 0..n), solve in FP64
+ *   [[A, P], [P^T, 0]] w~ = [phi(|p_i - x_Sj|)_j ; Y(p_i)],   w[i, :] = w~[0:n],
+ * A_jk = phi(|x_Sj - x_Sk|), P_jc = Y_c(x_Sj), Y = real orthonormal spherical harmonics
+ * of degree <= ell. Then the interpolant at p_i is sum_j w_ij f_Sj (the system is
+ * symmetric). Gaussian elimination with partial pivoting, one warp per point.
+ *   x: device N x 3; idx: device Nq x n; p: device Nq x 3; w: device Nq x n of w_dtype
+ *   (RBFSL_F64 or RBFSL_F32: FP64 solve, result rounded). status: device Nq or NULL
+ *   (RBFSL_ESINGULAR for a zero pivot; w row NaN).
+ * Errors: EINVAL (n < 1, ell > RBFSL_MAX_SH_DEGREE, n + (ell+1)^2 > RBFSL_MAX_SYSTEM,
+ *   kernel not RBFSL_PHS with odd p >= 1), ECUDA. */
+int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *idx, int64_t Nq, int n,
+                          int ell, int kernel, double kparam, const double *p, void *w,
+                          int w_dtype, int32_t *status, void *stream);
+
+/* Gather-dot (Algorithm 1, "interpolate q to the departure points"): for i < Nq, t < T,
+ *   q_out[i, t] = sum_j w[i, j] q[idx[i, j], t]           (w_dtype = q_dtype = RBFSL_F64)
+ *   q_out[i, t] = q[c, t] + sum_j w[i, j] (q[idx[i,j], t] - q[c, t]),  c = idx[i, 0]
+ *                                                          (w_dtype = q_dtype = RBFSL_F32)
+ * The difference form equals the first when sum_j w_ij = 1 and keeps FP32 rounding
+ * relative to the local variation of q. q_out may not alias q.
+ * Errors: EINVAL (mixed dtypes, T < 1, n < 1), ECUDA. */
+int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q,
+                     int T, int dtype, void *q_out, void *stream);
+
+/* ================================================================== context (Algorithm 1) */
+typedef struct rbfsl_ctx rbfsl_ctx;
+
+typedef struct rbfsl_stats {
+    int64_t steps_done;        /* SL steps completed since the last set_tracers */
+    int64_t singular_points;   /* cumulative per-point ESINGULAR flags */
+    int64_t knn_failures;      /* cumulative per-point EKNN flags */
+    int64_t uncovered_points;  /* cumulative EUNCOVERED flags (RBF-PU) */
+    double time;               /* model time of the current field */
+    size_t device_bytes;       /* device memory held by the context */
+} rbfsl_stats;
+
+/* Create a context on `device` whose work is enqueued on `stream` (a cudaStream_t of that
+ * device, or NULL for the legacy default stream). Errors: EINVAL, ECUDA. */
+int rbfsl_create(rbfsl_ctx **out, int device, void *stream);
+int rbfsl_destroy(rbfsl_ctx *ctx);
+
+/* Node set X (Sec. 3.1): N x 3 doubles on the host or the device, copied. Unit vectors
+ * are expected (not checked). Invalidates prepared state. */
+int rbfsl_set_nodes(rbfsl_ctx *ctx, const double *xyz, int64_t N, int mem);
+int rbfsl_set_velocity(rbfsl_ctx *ctx, int kind, const double *params, int nparams);
+int rbfsl_set_method(rbfsl_ctx *ctx, int method, int stencil_mode);
+/* Stencil size n (local) -- Sec. 2.2. */
+int rbfsl_set_stencil_size(rbfsl_ctx *ctx, int n);
+/* Spherical-harmonic degree ell of the augmentation (Sec. 2.4); ell < 0 selects the
+ * paper's rule ell = floor((sqrt(n) - 1) / 2). */
+int rbfsl_set_sh_degree(rbfsl_ctx *ctx, int ell);
+int rbfsl_set_kernel(rbfsl_ctx *ctx, int kind, double param);
+int rbfsl_set_precision(rbfsl_ctx *ctx, int precision);
+int rbfsl_set_dt(rbfsl_ctx *ctx, double dt);
+int rbfsl_set_time(rbfsl_ctx *ctx, double t);
+/* Initial field q(X, t): N x T, element type dtype (converted to the context precision),
+ * on the host (copied synchronously) or the device (copied on the context stream).
+ * Resets steps_done. */
+int rbfsl_set_tracers(rbfsl_ctx *ctx, const void *q, int64_t N, int T, int dtype, int mem);
+/* Run `nsteps` SL steps (Algorithm 1): departure points, interpolation, q <- q_Xi,
+ * t <- t + dt. Asynchronous on the context stream; prepares internal state on first use. */
+int rbfsl_step(rbfsl_ctx *ctx, int nsteps);
+/* Copy the current field (N x T) out as dtype to host (synchronises the stream) or device
+ * (enqueued on the stream). */
+int rbfsl_get_q(rbfsl_ctx *ctx, void *out, int dtype, int mem);
+/* Synchronise the stream and report counters (per-point failures are summed here). */
+int rbfsl_get_stats(rbfsl_ctx *ctx, rbfsl_stats *out);
+/* Debug views of the last step (device buffers owned by the context, valid until the next
+ * call that changes the context): departure points N x 3, stencils N x n, weights N x n
+ * (FP64 in RBFSL_FP64 mode, FP32 in RBFSL_MIXED). NULL where the method has none. */
+int rbfsl_last_step_buffers(rbfsl_ctx *ctx, const double **xi, const int32_t **idx,
+                            const void **w);
+/* Message of the last failed call on this context (thread-local when ctx is NULL). */
+const char *rbfsl_last_error(const rbfsl_ctx *ctx);
+const char *rbfsl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFSL_H */

@@ -1,0 +1,441 @@
+// Context API: the problem statement of Algorithm 1 (velocity, initial field, node set,
+// time step) and the SL time loop on the device. Every step of the loop runs in this
+// library's kernels; the host only validates, allocates and enqueues.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfsl {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+const char *get_error() { return g_err.c_str(); }
+
+// Accumulate per-point failure flags of one step into device counters.
+__global__ void count_status(const int32_t *__restrict__ st, int64_t N,
+                             unsigned long long *__restrict__ ctr) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int32_t s = i < N ? st[i] : 0;
+    const unsigned sing = __ballot_sync(0xffffffffu, s == RBFSL_ESINGULAR);
+    const unsigned knn = __ballot_sync(0xffffffffu, s == RBFSL_EKNN);
+    if ((threadIdx.x & 31) == 0) {
+        if (sing) atomicAdd(&ctr[0], (unsigned long long)__popc(sing));
+        if (knn) atomicAdd(&ctr[1], (unsigned long long)__popc(knn));
+    }
+}
+
+// CENTER mode: the stencil of each departure point is the stored stencil of its nearest node.
+__global__ void gather_center_stencils(const int32_t *__restrict__ K, const int32_t *__restrict__ Ik,
+                                       int64_t N, int n, int32_t *__restrict__ I) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * n) return;
+    const int64_t i = e / n;
+    const int j = (int)(e - i * n);
+    const int32_t k = K[i];
+    I[e] = k >= 0 ? Ik[(int64_t)k * n + j] : -1;
+}
+
+template <typename A, typename B>
+__global__ void convert_kernel(const A *__restrict__ in, B *__restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (B)in[i];
+}
+
+}  // namespace rbfsl
+
+using namespace rbfsl;
+
+struct rbfsl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // problem statement
+    int64_t N = 0;
+    double *X = nullptr;
+    int vel_kind = -1;
+    double vel[4] = {0, 0, 0, 0};
+    int method = RBFSL_LOCAL, mode = RBFSL_DIRECT;
+    int n = 0, ell = -1, kkind = RBFSL_PHS;
+    double kparam = 3.0;
+    int precision = RBFSL_FP64;
+    double dt = 0.0, t = 0.0;
+    int T = 0;
+    void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 by precision
+    int64_t steps_done = 0;
+    // prepared state (local method)
+    bool prepared = false;
+    rbfsl_knn_index *knn = nullptr;
+    double *xi = nullptr;
+    int32_t *I = nullptr, *K = nullptr, *Ik = nullptr, *status = nullptr;
+    void *W = nullptr;
+    unsigned long long *ctr = nullptr;  // [singular, knn failures]
+    size_t bytes = 0;
+};
+
+namespace {
+
+int fail(rbfsl_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    set_error(msg);
+    return code;
+}
+
+int ctx_cuda(rbfsl_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return RBFSL_OK;
+    return fail(c, e == cudaErrorMemoryAllocation ? RBFSL_ENOMEM : RBFSL_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CTX_TRY(c, expr)                                         \
+    do {                                                         \
+        int _rc = ctx_cuda((c), (expr), #expr);                  \
+        if (_rc != RBFSL_OK) return _rc;                         \
+    } while (0)
+
+#define CTX_RC(c, expr)                                          \
+    do {                                                         \
+        int _rc = (expr);                                        \
+        if (_rc != RBFSL_OK) return fail((c), _rc, get_error()); \
+    } while (0)
+
+template <typename P>
+int dalloc(rbfsl_ctx *c, P **p, size_t bytes) {
+    cudaError_t e = cudaMalloc((void **)p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, RBFSL_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->bytes += bytes;
+    return RBFSL_OK;
+}
+
+void release_prepared(rbfsl_ctx *c) {
+    if (c->knn) rbfsl_knn_index_destroy(c->knn);
+    c->knn = nullptr;
+    cudaFree(c->xi); cudaFree(c->I); cudaFree(c->K); cudaFree(c->Ik); cudaFree(c->status);
+    cudaFree(c->W); cudaFree(c->ctr);
+    c->xi = nullptr; c->I = c->K = c->Ik = c->status = nullptr; c->W = nullptr; c->ctr = nullptr;
+    c->prepared = false;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int effective_ell(const rbfsl_ctx *c) {
+    if (c->ell >= 0) return c->ell;
+    return (int)std::floor(0.5 * (std::sqrt((double)c->n) - 1.0));
+}
+
+int prepare(rbfsl_ctx *c) {
+    if (c->prepared) return RBFSL_OK;
+    if (!c->X) return fail(c, RBFSL_ENOTCONF, "set_nodes has not been called");
+    if (c->vel_kind < 0) return fail(c, RBFSL_ENOTCONF, "set_velocity has not been called");
+    if (!(c->dt > 0)) return fail(c, RBFSL_ENOTCONF, "set_dt has not been called");
+    if (!c->q) return fail(c, RBFSL_ENOTCONF, "set_tracers has not been called");
+    if (c->method != RBFSL_LOCAL)
+        return fail(c, RBFSL_EINVAL, "only the local method is available in this build");
+    if (c->n < 1 || c->n > c->N) return fail(c, RBFSL_ENOTCONF, "stencil size not set or > N");
+    const int ell = effective_ell(c);
+    if (ell > RBFSL_MAX_SH_DEGREE || c->n + (ell + 1) * (ell + 1) > RBFSL_MAX_SYSTEM)
+        return fail(c, RBFSL_EINVAL, "n + (ell+1)^2 exceeds RBFSL_MAX_SYSTEM");
+    const int pw = (int)c->kparam;
+    if (c->kkind != RBFSL_PHS || pw < 1 || !(pw & 1))
+        return fail(c, RBFSL_EINVAL, "local stencils need the PHS kernel with odd power");
+    const int64_t N = c->N, n = c->n;
+    int rc;
+    if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->I, N * n * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->status, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->W, N * n * (c->precision == RBFSL_FP64 ? 8 : 4)))) return rc;
+    if ((rc = dalloc(c, &c->ctr, 2 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 2 * sizeof(unsigned long long), c->stream));
+    CTX_RC(c, rbfsl_knn_index_create(&c->knn, c->X, N, (int)n, c->stream));
+    c->bytes += c->knn->bytes;
+    if (c->mode == RBFSL_CENTER) {
+        if ((rc = dalloc(c, &c->K, N * sizeof(int32_t)))) return rc;
+        if ((rc = dalloc(c, &c->Ik, N * n * sizeof(int32_t)))) return rc;
+        // stencil of node k: x_k and its n-1 nearest neighbours (Sec. 2.2)
+        CTX_RC(c, launch_knn(c->knn, c->X, N, (int)n, c->Ik, c->status, c->stream));
+    }
+    c->prepared = true;
+    return RBFSL_OK;
+}
+
+int one_step(rbfsl_ctx *c) {
+    const int64_t N = c->N;
+    const int n = c->n, ell = effective_ell(c), pw = (int)c->kparam;
+    const double t1 = c->t + c->dt;
+    const int wdt = c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32;
+    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    if (c->mode == RBFSL_DIRECT) {
+        CTX_RC(c, launch_knn(c->knn, c->xi, N, n, c->I, c->status, c->stream));
+    } else {
+        CTX_RC(c, launch_knn(c->knn, c->xi, N, 1, c->K, c->status, c->stream));
+        const int64_t tot = N * n;
+        gather_center_stencils<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->K, c->Ik, N, n, c->I);
+        CTX_RC(c, launch_status("gather_center_stencils"));
+    }
+    CTX_RC(c, launch_weights(c->X, c->I, N, n, ell, pw, c->xi, c->W, wdt, c->status, c->stream));
+    count_status<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->status, N, c->ctr);
+    CTX_RC(c, launch_gather(c->I, c->W, N, n, c->q, c->T, wdt, c->q_next, c->stream));
+    std::swap(c->q, c->q_next);
+    c->t = t1;
+    ++c->steps_done;
+    return RBFSL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rbfsl_version(void) { return "rbfsl-gb300 0.1 (sm_103a)"; }
+
+const char *rbfsl_last_error(const rbfsl_ctx *c) { return c ? c->err.c_str() : get_error(); }
+
+int rbfsl_create(rbfsl_ctx **out, int device, void *stream) {
+    RBFSL_CHECK_ARG(out != nullptr, "create: out is null");
+    int ndev = 0;
+    RBFSL_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    RBFSL_CHECK_ARG(device >= 0 && device < ndev, "create: no such device");
+    auto *c = new rbfsl_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    DeviceGuard g(device);
+    int rc = sh_tables_init();
+    if (rc != RBFSL_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return RBFSL_OK;
+}
+
+int rbfsl_destroy(rbfsl_ctx *c) {
+    if (!c) return RBFSL_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    cudaFree(c->X); cudaFree(c->q); cudaFree(c->q_next);
+    delete c;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_nodes(rbfsl_ctx *c, const double *xyz, int64_t N, int mem) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!xyz || N < 1 || N >= ((int64_t)1 << 31) || (mem != RBFSL_HOST && mem != RBFSL_DEVICE))
+        return fail(c, RBFSL_EINVAL, "set_nodes: bad arguments");
+    DeviceGuard g(c->device);
+    CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    release_prepared(c);
+    cudaFree(c->X); c->X = nullptr;
+    cudaFree(c->q); cudaFree(c->q_next); c->q = c->q_next = nullptr;
+    c->bytes = 0;
+    c->N = N;
+    int rc = dalloc(c, &c->X, N * 3 * sizeof(double));
+    if (rc) return rc;
+    CTX_TRY(c, cudaMemcpyAsync(c->X, xyz, N * 3 * sizeof(double),
+                               mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                               c->stream));
+    CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    return RBFSL_OK;
+}
+
+int rbfsl_set_velocity(rbfsl_ctx *c, int kind, const double *params, int nparams) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!params) return fail(c, RBFSL_EINVAL, "set_velocity: params is null");
+    if (kind == RBFSL_VEL_RIGID) {
+        if (nparams != 4) return fail(c, RBFSL_EINVAL, "rigid rotation takes 4 parameters");
+        const double a = std::sqrt(params[0] * params[0] + params[1] * params[1] + params[2] * params[2]);
+        if (!(std::fabs(a - 1.0) < 1e-12)) return fail(c, RBFSL_EINVAL, "rotation axis is not a unit vector");
+    } else if (kind == RBFSL_VEL_DEFORM_Y2) {
+        if (nparams != 2 || !(params[1] > 0)) return fail(c, RBFSL_EINVAL, "deformation takes {kappa, T_f > 0}");
+    } else {
+        return fail(c, RBFSL_EINVAL, "unknown velocity kind");
+    }
+    c->vel_kind = kind;
+    for (int i = 0; i < 4; ++i) c->vel[i] = i < nparams ? params[i] : 0.0;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_method(rbfsl_ctx *c, int method, int stencil_mode) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (method < RBFSL_LOCAL || method > RBFSL_PU) return fail(c, RBFSL_EINVAL, "unknown method");
+    if (stencil_mode != RBFSL_DIRECT && stencil_mode != RBFSL_CENTER)
+        return fail(c, RBFSL_EINVAL, "unknown stencil mode");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    c->method = method;
+    c->mode = stencil_mode;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_stencil_size(rbfsl_ctx *c, int n) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (n < 1) return fail(c, RBFSL_EINVAL, "stencil size must be >= 1");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    c->n = n;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_sh_degree(rbfsl_ctx *c, int ell) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (ell > RBFSL_MAX_SH_DEGREE) return fail(c, RBFSL_EINVAL, "ell > RBFSL_MAX_SH_DEGREE");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    c->ell = ell;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_kernel(rbfsl_ctx *c, int kind, double param) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (kind < RBFSL_PHS || kind > RBFSL_IMQ || !(param > 0)) return fail(c, RBFSL_EINVAL, "bad kernel");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    c->kkind = kind;
+    c->kparam = param;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_precision(rbfsl_ctx *c, int precision) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (precision != RBFSL_FP64 && precision != RBFSL_MIXED) return fail(c, RBFSL_EINVAL, "unknown precision");
+    if (precision == c->precision) return RBFSL_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+    cudaFree(c->q); cudaFree(c->q_next);
+    c->q = c->q_next = nullptr;  // the field must be set again in the new precision
+    c->T = 0;
+    c->precision = precision;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_dt(rbfsl_ctx *c, double dt) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(c, RBFSL_EINVAL, "dt must be positive");
+    c->dt = dt;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_time(rbfsl_ctx *c, double t) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!std::isfinite(t)) return fail(c, RBFSL_EINVAL, "time must be finite");
+    c->t = t;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, int mem) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!c->X) return fail(c, RBFSL_ENOTCONF, "set_nodes must come before set_tracers");
+    if (!q || N != c->N || T < 1 || (dtype != RBFSL_F64 && dtype != RBFSL_F32) ||
+        (mem != RBFSL_HOST && mem != RBFSL_DEVICE))
+        return fail(c, RBFSL_EINVAL, "set_tracers: bad arguments");
+    DeviceGuard g(c->device);
+    const int es = c->precision == RBFSL_FP64 ? 8 : 4;
+    const int64_t cnt = N * (int64_t)T;
+    if (T != c->T || !c->q) {
+        CTX_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->q); cudaFree(c->q_next);
+        c->q = c->q_next = nullptr;
+        int rc;
+        if ((rc = dalloc(c, &c->q, cnt * es))) return rc;
+        if ((rc = dalloc(c, &c->q_next, cnt * es))) return rc;
+        c->T = T;
+    }
+    const int in_es = dtype == RBFSL_F64 ? 8 : 4;
+    const unsigned blocks = (unsigned)((cnt + 255) / 256);
+    if (in_es == es) {
+        CTX_TRY(c, cudaMemcpyAsync(c->q, q, cnt * es,
+                                   mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    } else {
+        // stage the caller's type in q_next, convert into q
+        CTX_TRY(c, cudaMemcpyAsync(c->q_next, q, cnt * in_es,
+                                   mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        if (in_es == 8) convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double *)c->q_next, (float *)c->q, cnt);
+        else convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q_next, (double *)c->q, cnt);
+        CTX_RC(c, launch_status("set_tracers convert"));
+    }
+    if (mem == RBFSL_HOST) CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    c->steps_done = 0;
+    return RBFSL_OK;
+}
+
+int rbfsl_step(rbfsl_ctx *c, int nsteps) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (nsteps < 0) return fail(c, RBFSL_EINVAL, "nsteps < 0");
+    DeviceGuard g(c->device);
+    int rc = prepare(c);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s)
+        if ((rc = one_step(c))) return rc;
+    return RBFSL_OK;
+}
+
+int rbfsl_get_q(rbfsl_ctx *c, void *out, int dtype, int mem) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!c->q) return fail(c, RBFSL_ENOTCONF, "no tracers");
+    if (!out || (dtype != RBFSL_F64 && dtype != RBFSL_F32) || (mem != RBFSL_HOST && mem != RBFSL_DEVICE))
+        return fail(c, RBFSL_EINVAL, "get_q: bad arguments");
+    DeviceGuard g(c->device);
+    const int es = c->precision == RBFSL_FP64 ? 8 : 4;
+    const int out_es = dtype == RBFSL_F64 ? 8 : 4;
+    const int64_t cnt = c->N * (int64_t)c->T;
+    const cudaMemcpyKind kind = mem == RBFSL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (es == out_es) {
+        CTX_TRY(c, cudaMemcpyAsync(out, c->q, cnt * es, kind, c->stream));
+    } else {
+        const unsigned blocks = (unsigned)((cnt + 255) / 256);
+        if (es == 8) convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double *)c->q, (float *)c->q_next, cnt);
+        else convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q, (double *)c->q_next, cnt);
+        CTX_RC(c, launch_status("get_q convert"));
+        CTX_TRY(c, cudaMemcpyAsync(out, c->q_next, cnt * out_es, kind, c->stream));
+    }
+    if (mem == RBFSL_HOST) CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    return RBFSL_OK;
+}
+
+int rbfsl_get_stats(rbfsl_ctx *c, rbfsl_stats *out) {
+    if (!c || !out) return fail(c, RBFSL_EINVAL, "get_stats: null argument");
+    DeviceGuard g(c->device);
+    CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    std::memset(out, 0, sizeof(*out));
+    if (c->ctr) {
+        unsigned long long h[2] = {0, 0};
+        CTX_TRY(c, cudaMemcpy(h, c->ctr, sizeof(h), cudaMemcpyDeviceToHost));
+        out->singular_points = (int64_t)h[0];
+        out->knn_failures = (int64_t)h[1];
+    }
+    out->steps_done = c->steps_done;
+    out->time = c->t;
+    out->device_bytes = c->bytes;
+    return RBFSL_OK;
+}
+
+int rbfsl_last_step_buffers(rbfsl_ctx *c, const double **xi, const int32_t **idx, const void **w) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (xi) *xi = c->xi;
+    if (idx) *idx = c->I;
+    if (w) *w = c->W;
+    return RBFSL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Gather-dot W.q (Algorithm 1, "interpolate q^m to the departure points"): for each output
+// row i, q_out[i, :] = sum_j w[i, j] q[idx[i, j], :]. Memory-bound: per row it streams n
+// weights and n indices once and gathers n rows of q (T contiguous values each, so a row
+// group of lanes reads whole rows coalesced).
+//
+// A row group of L lanes (L = the power of two >= min(T, 32)) serves one output row; the
+// group's first n (w, idx) pairs are loaded cooperatively, one per lane, and broadcast with
+// warp shuffles. FP32 uses the difference form q_c + sum_j w_j (q_j - q_c), c = idx[i, 0].
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfsl {
+
+template <typename R, bool kDiff>
+__global__ void __launch_bounds__(256) gather_dot_kernel(const int32_t *__restrict__ idx,
+                                                         const R *__restrict__ W, int64_t Nq,
+                                                         int n, const R *__restrict__ q, int T,
+                                                         int L, R *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rows_per_warp = kWarp / L;
+    const int sub = lane % L, grp = lane / L;
+    const int64_t i = gwarp * rows_per_warp + grp;
+    const bool active = i < Nq;
+    if (__all_sync(0xffffffffu, !active)) return;
+    for (int t0 = 0; t0 < T; t0 += L) {
+        const int t = t0 + sub;
+        R acc = R(0), qc = R(0);
+        if (kDiff && active && t < T) {
+            const int c = idx[i * n];
+            qc = c >= 0 ? q[(int64_t)c * T + t] : R(NAN);
+        }
+        for (int j0 = 0; j0 < n; j0 += L) {
+            // cooperative load of up to L (w, idx) pairs of row i
+            R wj = R(0);
+            int sj = 0;
+            if (active && j0 + sub < n) {
+                wj = W[i * n + j0 + sub];
+                sj = idx[i * n + j0 + sub];
+            }
+            const int cnt = min(L, n - j0);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const R w = __shfl_sync(0xffffffffu, wj, grp * L + jj);
+                const int s = __shfl_sync(0xffffffffu, sj, grp * L + jj);
+                if (active && t < T) {
+                    const R v = s >= 0 ? q[(int64_t)s * T + t] : R(NAN);  // failed stencil
+                    acc = fma(w, kDiff ? (v - qc) : v, acc);
+                }
+            }
+        }
+        if (active && t < T) out[i * T + t] = kDiff ? qc + acc : acc;
+    }
+}
+
+int launch_gather(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q, int T,
+                  int dtype, void *q_out, cudaStream_t s) {
+    if (Nq == 0) return RBFSL_OK;
+    int L = 1;
+    while (L < T && L < 32) L <<= 1;
+    const int rows_per_warp = kWarp / L;
+    const int threads = 256;
+    const int64_t warps = (Nq + rows_per_warp - 1) / rows_per_warp;
+    const unsigned blocks = (unsigned)((warps * kWarp + threads - 1) / threads);
+    if (dtype == RBFSL_F64)
+        gather_dot_kernel<double, false><<<blocks, threads, 0, s>>>(
+            idx, (const double *)w, Nq, n, (const double *)q, T, L, (double *)q_out);
+    else
+        gather_dot_kernel<float, true><<<blocks, threads, 0, s>>>(
+            idx, (const float *)w, Nq, n, (const float *)q, T, L, (float *)q_out);
+    return launch_status("gather_dot");
+}
+
+}  // namespace rbfsl
+
+extern "C" int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, int n,
+                                const void *q, int T, int dtype, void *q_out, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(Nq >= 0 && n >= 1 && T >= 1, "gather_dot: bad sizes");
+    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32, "gather_dot: bad dtype");
+    RBFSL_CHECK_ARG(Nq == 0 || (idx && w && q && q_out), "gather_dot: null pointer");
+    RBFSL_CHECK_ARG(q != q_out, "gather_dot: q_out aliases q");
+    return launch_gather(idx, w, Nq, n, q, T, dtype, q_out, (cudaStream_t)stream);
+}

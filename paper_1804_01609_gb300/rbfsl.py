@@ -1,0 +1,303 @@
+"""Thin Python binding of librbfsl (include/rbfsl.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls. Tensors are torch tensors
+on the CUDA device (PyTorch provides device memory and streams); all computation happens
+in the library's kernels. There is no fallback: if the CUDA library is missing or fails to
+load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOTCONF, ENOMEM, ESINGULAR, EUNCOVERED, ETIMEDOUT, ECUDA, EKNN = 0, -1, -2, -3, -4, -5, -6, -7, -8
+VEL_RIGID, VEL_DEFORM_Y2 = 0, 1
+LOCAL, GLOBAL, PU = 0, 1, 2
+DIRECT, CENTER = 0, 1
+PHS, GAUSS, IMQ = 0, 1, 2
+FP64, MIXED = 0, 1
+F64, F32 = 0, 1
+HOST, DEVICE = 0, 1
+
+_NAMES = {OK: "OK", EINVAL: "EINVAL", ENOTCONF: "ENOTCONF", ENOMEM: "ENOMEM",
+          ESINGULAR: "ESINGULAR", EUNCOVERED: "EUNCOVERED", ETIMEDOUT: "ETIMEDOUT",
+          ECUDA: "ECUDA", EKNN: "EKNN"}
+
+
+class RbfslError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps_done", ctypes.c_int64), ("singular_points", ctypes.c_int64),
+                ("knn_failures", ctypes.c_int64), ("uncovered_points", ctypes.c_int64),
+                ("time", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+SIGNATURES = {
+    "rbfsl_version": (ctypes.c_char_p, []),
+    "rbfsl_last_error": (ctypes.c_char_p, [_P]),
+    "rbfsl_trace_rk4": (_I, [_P, _I64, _I, _P, _D, _D, _I, _P, _P]),
+    "rbfsl_knn_index_create": (_I, [_P, _P, _I64, _I, _P]),
+    "rbfsl_knn_index_destroy": (_I, [_P]),
+    "rbfsl_knn_query": (_I, [_P, _P, _I64, _I, _P, _P, _P]),
+    "rbfsl_stencil_weights": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _D, _P, _P, _I, _P, _P]),
+    "rbfsl_gather_dot": (_I, [_P, _P, _I64, _I, _P, _I, _I, _P, _P]),
+    "rbfsl_create": (_I, [_P, _I, _P]),
+    "rbfsl_destroy": (_I, [_P]),
+    "rbfsl_set_nodes": (_I, [_P, _P, _I64, _I]),
+    "rbfsl_set_velocity": (_I, [_P, _I, _P, _I]),
+    "rbfsl_set_method": (_I, [_P, _I, _I]),
+    "rbfsl_set_stencil_size": (_I, [_P, _I]),
+    "rbfsl_set_sh_degree": (_I, [_P, _I]),
+    "rbfsl_set_kernel": (_I, [_P, _I, _D]),
+    "rbfsl_set_precision": (_I, [_P, _I]),
+    "rbfsl_set_dt": (_I, [_P, _D]),
+    "rbfsl_set_time": (_I, [_P, _D]),
+    "rbfsl_set_tracers": (_I, [_P, _P, _I64, _I, _I, _I]),
+    "rbfsl_step": (_I, [_P, _I]),
+    "rbfsl_get_q": (_I, [_P, _P, _I, _I]),
+    "rbfsl_get_stats": (_I, [_P, _P]),
+    "rbfsl_last_step_buffers": (_I, [_P, _P, _P, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load librbfsl.so (building it first if asked); raises if it cannot be loaded."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run build() first")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != OK:
+        msg = load().rbfsl_last_error(ctx)
+        raise RbfslError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+# --------------------------------------------------------------------------- stateless ops
+def rbfsl_trace_rk4(x, vel_kind, vel_params, t1, dt, precision, xi, stream=None):
+    prm = np.ascontiguousarray(vel_params, dtype=np.float64)
+    _check(load().rbfsl_trace_rk4(_ptr(x), x.shape[0], vel_kind, prm.ctypes.data, t1, dt,
+                                  precision, _ptr(xi), _stream(stream)))
+
+
+class KnnIndex:
+    def __init__(self, x, k_hint, stream=None):
+        self._h = ctypes.c_void_p()
+        self.N = x.shape[0]
+        _check(load().rbfsl_knn_index_create(ctypes.byref(self._h), _ptr(x), x.shape[0],
+                                             k_hint, _stream(stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().rbfsl_knn_index_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rbfsl_knn_index_create(x, k_hint, stream=None) -> KnnIndex:
+    return KnnIndex(x, k_hint, stream)
+
+
+def rbfsl_knn_query(index, q, k, idx, status=None, stream=None):
+    _check(load().rbfsl_knn_query(index.handle, _ptr(q), q.shape[0], k, _ptr(idx),
+                                  _ptr(status), _stream(stream)))
+
+
+def rbfsl_stencil_weights(x, idx, n, ell, kernel, kparam, p, w, status=None, stream=None):
+    _check(load().rbfsl_stencil_weights(_ptr(x), x.shape[0], _ptr(idx), p.shape[0], n, ell,
+                                        kernel, float(kparam), _ptr(p), _ptr(w), _dtype_code(w),
+                                        _ptr(status), _stream(stream)))
+
+
+def rbfsl_gather_dot(idx, w, q, q_out, stream=None):
+    T = q.shape[1] if q.dim() == 2 else 1
+    _check(load().rbfsl_gather_dot(_ptr(idx), _ptr(w), idx.shape[0], idx.shape[1], _ptr(q), T,
+                                   _dtype_code(q), _ptr(q_out), _stream(stream)))
+
+
+# --------------------------------------------------------------------------- context
+class Context:
+    """Algorithm 1 on the device: set the problem, then step. Method names follow the C ABI
+    (rbfsl_set_nodes -> set_nodes, ...)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        self.stream = _stream(stream) if stream is not None else 0
+        _check(load().rbfsl_create(ctypes.byref(self._h), device, self.stream))
+        self.N = 0
+        self.T = 0
+
+    def _c(self, rc):
+        return _check(rc, self._h)
+
+    def close(self):
+        if self._h:
+            load().rbfsl_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_nodes(self, X):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            self._c(load().rbfsl_set_nodes(self._h, X.ctypes.data, X.shape[0], HOST))
+        else:
+            self._c(load().rbfsl_set_nodes(self._h, _ptr(X), X.shape[0], DEVICE))
+        self.N = X.shape[0]
+
+    def set_velocity(self, kind, params):
+        prm = np.ascontiguousarray(params, dtype=np.float64)
+        self._c(load().rbfsl_set_velocity(self._h, kind, prm.ctypes.data, prm.size))
+
+    def set_method(self, method, stencil_mode=DIRECT):
+        self._c(load().rbfsl_set_method(self._h, method, stencil_mode))
+
+    def set_stencil_size(self, n):
+        self._c(load().rbfsl_set_stencil_size(self._h, n))
+
+    def set_sh_degree(self, ell):
+        self._c(load().rbfsl_set_sh_degree(self._h, ell))
+
+    def set_kernel(self, kind, param):
+        self._c(load().rbfsl_set_kernel(self._h, kind, float(param)))
+
+    def set_precision(self, prec):
+        self._c(load().rbfsl_set_precision(self._h, prec))
+
+    def set_dt(self, dt):
+        self._c(load().rbfsl_set_dt(self._h, float(dt)))
+
+    def set_time(self, t):
+        self._c(load().rbfsl_set_time(self._h, float(t)))
+
+    def set_tracers(self, q):
+        if isinstance(q, np.ndarray):
+            q2 = np.ascontiguousarray(q.reshape(q.shape[0], -1))
+            code = F64 if q2.dtype == np.float64 else F32
+            if q2.dtype not in (np.float64, np.float32):
+                q2 = q2.astype(np.float64); code = F64
+            self._c(load().rbfsl_set_tracers(self._h, q2.ctypes.data, q2.shape[0], q2.shape[1], code, HOST))
+            self.T = q2.shape[1]
+        else:
+            q2 = q.reshape(q.shape[0], -1)
+            dev = DEVICE if q2.is_cuda else HOST
+            self._c(load().rbfsl_set_tracers(self._h, _ptr(q2), q2.shape[0], q2.shape[1],
+                                             _dtype_code(q2), dev))
+            self.T = q2.shape[1]
+
+    def step(self, nsteps=1):
+        self._c(load().rbfsl_step(self._h, nsteps))
+
+    def get_q(self, out=None, dtype=np.float64):
+        if out is None:
+            out = np.empty((self.N, self.T), dtype=dtype)
+        if isinstance(out, np.ndarray):
+            code = F64 if out.dtype == np.float64 else F32
+            self._c(load().rbfsl_get_q(self._h, out.ctypes.data, code, HOST))
+        else:
+            self._c(load().rbfsl_get_q(self._h, _ptr(out), _dtype_code(out),
+                                       DEVICE if out.is_cuda else HOST))
+        return out
+
+    def get_stats(self) -> Stats:
+        s = Stats()
+        self._c(load().rbfsl_get_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def last_step_buffers(self):
+        xi, idx, w = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        self._c(load().rbfsl_last_step_buffers(self._h, ctypes.byref(xi), ctypes.byref(idx), ctypes.byref(w)))
+        return xi.value, idx.value, w.value
+
+    def last_step_tensors(self, n, weights_dtype):
+        """Copies of the last step's departure points (N x 3), stencils (N x n) and
+        weights (N x n, weights_dtype) as torch tensors."""
+        import torch
+        xi, idx, w = self.last_step_buffers()
+        torch.cuda.synchronize()
+        wt = "<f8" if weights_dtype == torch.float64 else "<f4"
+        out = []
+        for ptr, shape, ts in ((xi, (self.N, 3), "<f8"), (idx, (self.N, n), "<i4"), (w, (self.N, n), wt)):
+            out.append(None if not ptr else torch.as_tensor(_DeviceView(ptr, shape, ts), device="cuda").clone())
+        return tuple(out)
+
+
+class _DeviceView:
+    """Exposes a library-owned device buffer through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (int(ptr), False), "shape": tuple(shape),
+                                         "typestr": typestr, "strides": None, "version": 3}
