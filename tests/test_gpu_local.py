@@ -6,10 +6,13 @@ Tolerances (FP64 unless stated):
   k-NN                    bit-exact indices vs brute force on the same points
   weights, n=31 ell=2     1e-10 relative to max|w| (the benchmark spec's bound; FP64 weights are
                           determined to ~3e-13 at this size)
-  weights, n=84 ell=4     the saddle-point systems have cond ~1e18, so two FP64 solvers
-                          agree only to ~1e-5..1e-3 on w; parity is checked on what FP64 does
-                          fix: sum w = 1 and spherical-harmonic reproduction to 1e-11 of the
-                          weights' scale, and interpolated smooth fields to 1e-9 of max|q|
+  weights, n=84 ell=4     the saddle-point systems have cond ~1e18: moving the nodes by one
+                          ulp changes the weights by ~1e-6..1e-3, so two FP64 solvers cannot
+                          agree beyond that. Parity is checked on what FP64 does fix: sum w = 1
+                          and spherical-harmonic reproduction to 1e-11 of the weights' scale,
+                          and interpolated fields within 5x the oracle's own FP64 noise floor
+                          (the largest change of the oracle's interpolated values when every
+                          node coordinate moves by one ulp), plus 1e-12 of max|q|
   fields after S steps    1e-10 relative l2 at n=31 (cfg 1 literal bound)
 """
 import math
@@ -97,6 +100,24 @@ def test_knn_empty_and_bad_k():
         rbfsl.rbfsl_knn_query(ix, _t(X), 101, torch.empty((100, 101), dtype=torch.int32, device=DEV))
 
 
+def perturb_one_ulp(X, seed=0):
+    """Every coordinate moved by one ulp in a random direction."""
+    s = np.random.default_rng(seed).choice([-1.0, 1.0], size=X.shape)
+    return np.nextafter(X, X + s)
+
+
+def assert_within_noise_floor(orc, X, I, P, q, got, ell, p, factor=5.0, nrows=300):
+    """got[r] (interpolated values at P[r] on stencil I[r]) must match the oracle within
+    `factor` times the oracle's own sensitivity to a one-ulp move of the node coordinates."""
+    rows = np.arange(min(nrows, len(P)))
+    Xp = perturb_one_ulp(X)
+    ref = np.stack([orc.stencil_weights(X, I[r], ell, orc.PHS, float(p), P[r]) @ q[I[r]] for r in rows])
+    alt = np.stack([orc.stencil_weights(Xp, I[r], ell, orc.PHS, float(p), P[r]) @ q[I[r]] for r in rows])
+    floor = np.abs(alt - ref).max()
+    diff = np.abs(got[rows] - ref).max()
+    assert diff <= factor * floor + 1e-12 * np.abs(q).max(), (diff, floor)
+
+
 def _departures(X, seed, scale=0.6):
     rng = np.random.default_rng(seed)
     P = X + rng.normal(scale=scale / math.sqrt(X.shape[0]), size=X.shape)
@@ -135,12 +156,11 @@ def test_weights_invariants_and_interpolation(orc, N, n, ell, p):
         assert abs(W[i].sum() - 1.0) < 1e-11 * scale
         Ys = orc.sh_eval(ell, X[I[i]])
         np.testing.assert_allclose(W[i] @ Ys, orc.sh_eval(ell, P[i]), atol=1e-11 * scale * np.abs(Ys).max())
-    # interpolation of smooth fields agrees with the oracle's FP64 weights
+    # interpolation of smooth fields agrees with the oracle within its FP64 noise floor
     wl = inputs.config_local_deformation(N=N, n_random=4)
     q = wl.tracers(X)
-    ref = orc.local_apply(X, P[rows], q, n, ell, orc.PHS, float(p))
     got = np.einsum("ij,ijt->it", W[rows], q[I[rows]])
-    assert np.abs(got - ref).max() < 1e-9 * np.abs(q).max()
+    assert_within_noise_floor(orc, X, I[rows], P[rows], q, got, ell, p)
 
 
 @pytest.mark.parametrize("T", [1, 5, 33, 64])
@@ -226,8 +246,7 @@ def test_cfg2_full_size_sampled_step(orc, cfg2):
     assert np.abs(Xi - ref_xi).max() < 1e-14
     rows = np.sort(np.random.default_rng(0).choice(N, 1000, replace=False))
     np.testing.assert_array_equal(I.cpu().numpy()[rows], orc.knn(w.X, Xi[rows], n))
-    ref = orc.local_apply(w.X, Xi[rows], q1, n, w.ell, orc.PHS, float(w.power))
-    assert np.abs(q2[rows] - ref).max() < 1e-9 * np.abs(q1).max()
+    assert_within_noise_floor(orc, w.X, I.cpu().numpy()[rows], Xi[rows], q1, q2[rows], w.ell, w.power)
     st = ctx.get_stats()
     assert st.singular_points == 0 and st.knn_failures == 0
     ctx.close()
