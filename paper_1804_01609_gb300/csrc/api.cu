@@ -85,6 +85,7 @@ int fail(rbfsl_ctx *c, int code, const std::string &msg) {
 
 int ctx_cuda(rbfsl_ctx *c, cudaError_t e, const char *what) {
     if (e == cudaSuccess) return RBFSL_OK;
+    cudaGetLastError();  // clear the runtime's record so later launches are not blamed
     return fail(c, e == cudaErrorMemoryAllocation ? RBFSL_ENOMEM : RBFSL_ECUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -355,8 +356,10 @@ int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, 
         cudaFree(c->q); cudaFree(c->q_next);
         c->q = c->q_next = nullptr;
         int rc;
-        if ((rc = dalloc(c, &c->q, cnt * es))) return rc;
-        if ((rc = dalloc(c, &c->q_next, cnt * es))) return rc;
+        // 8 bytes per element whatever the precision: either buffer can stage the other
+        // element type during the conversions of set_tracers / get_q.
+        if ((rc = dalloc(c, &c->q, cnt * 8))) return rc;
+        if ((rc = dalloc(c, &c->q_next, cnt * 8))) return rc;
         c->T = T;
     }
     const int in_es = dtype == RBFSL_F64 ? 8 : 4;

@@ -19,6 +19,7 @@ const char *get_error();
     do {                                                                                   \
         cudaError_t _e = (expr);                                                           \
         if (_e != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
             ::rbfsl::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));        \
             return RBFSL_ECUDA;                                                            \
         }                                                                                  \
