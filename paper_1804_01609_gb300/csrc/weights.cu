@@ -185,6 +185,143 @@ __global__ void __launch_bounds__(128) weights_direct_kernel(WeightsArgs a, WT *
     if (a.status && lane == 0) a.status[i] = RBFSL_OK;
 }
 
+// Four warps per point, for systems too large to give every SM sub-partition its own warp
+// with one warp per point (m > ~70: one m x (m+1) FP64 matrix is ~40-100 KB). Each SM
+// sub-partition has its own FP64 unit, so the elimination is spread over 4 warps: warp 0
+// picks the pivot, swaps and scales the column; then all warps update the trailing rows
+// (row-cyclic over warps, lanes over columns, pivot row in registers).
+constexpr int kCtaWarps = 4;
+
+template <typename WT>
+__global__ void __launch_bounds__(kCtaWarps * 32) weights_cta_kernel(WeightsArgs a, WT *__restrict__ W) {
+    extern __shared__ double smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t i = blockIdx.x;
+    const int n = a.n, m = a.m, ld = a.ld, M = m - n;
+    double *A = smem;
+    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n;
+    __shared__ int s_flag;
+
+    if (tid == 0) s_flag = 0;
+    __syncthreads();
+    for (int j = tid; j < n; j += kCtaWarps * kWarp) {
+        const int64_t s = a.idx[i * n + j];
+        if (s < 0) { s_flag = 1; continue; }
+        cx[j] = a.X[3 * s];
+        cy[j] = a.X[3 * s + 1];
+        cz[j] = a.X[3 * s + 2];
+    }
+    __syncthreads();
+    if (s_flag) {
+        for (int j = tid; j < n; j += kCtaWarps * kWarp) W[i * n + j] = (WT)NAN;
+        if (a.status && tid == 0) a.status[i] = RBFSL_EKNN;
+        return;
+    }
+    const double px = a.P[3 * i], py = a.P[3 * i + 1], pz = a.P[3 * i + 2];
+
+    // ---- assembly
+    for (int r = warp; r < n; r += kCtaWarps) {
+        const double xr = cx[r], yr = cy[r], zr = cz[r];
+        if (lane == 0) A[r * ld + r] = 0.0;
+        for (int c = r + 1 + lane; c < n; c += kWarp) {
+            const double dx = xr - cx[c], dy = yr - cy[c], dz = zr - cz[c];
+            const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
+            A[r * ld + c] = v;
+            A[c * ld + r] = v;
+        }
+    }
+    for (int j = tid; j < n; j += kCtaWarps * kWarp) {
+        sh_eval(a.ell, cx[j], cy[j], cz[j], [&](int c, double v) {
+            A[j * ld + n + c] = v;
+            A[(n + c) * ld + j] = v;
+        });
+        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
+        A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
+    }
+    for (int e = tid; e < M * M; e += kCtaWarps * kWarp) A[(n + e / M) * ld + n + e % M] = 0.0;
+    if (tid == 0) sh_eval(a.ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
+    __syncthreads();
+
+    // ---- Gaussian elimination with partial pivoting on [A~ | b]
+    for (int k = 0; k < m; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bidx = m;
+            for (int r = k + lane; r < m; r += kWarp) {
+                const double v = fabs(A[r * ld + k]);
+                if (v > best) { best = v; bidx = r; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+                if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+            }
+            if (!(best > 0.0) || !isfinite(best)) {
+                if (lane == 0) s_flag = 2;
+            } else {
+                if (bidx != k) {
+                    for (int c = k + lane; c <= m; c += kWarp) {
+                        const double t = A[k * ld + c];
+                        A[k * ld + c] = A[bidx * ld + c];
+                        A[bidx * ld + c] = t;
+                    }
+                    __syncwarp();
+                }
+                const double inv = 1.0 / A[k * ld + k];
+                for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
+            }
+        }
+        __syncthreads();
+        if (s_flag) break;
+        const int ncols = m - k;
+        double pk[5];
+        int jc[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            jc[c] = k + 1 + lane + c * kWarp;
+            pk[c] = (c * kWarp < ncols && jc[c] <= m) ? A[k * ld + jc[c]] : 0.0;
+        }
+        const int nch = (ncols + kWarp - 1) / kWarp;
+        int r = k + 1 + warp;
+        for (; r + kCtaWarps < m; r += 2 * kCtaWarps) {
+            const int r1 = r + kCtaWarps;
+            const double l0 = A[r * ld + k], l1 = A[r1 * ld + k];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                if (c < nch && jc[c] <= m) {
+                    const double v0 = A[r * ld + jc[c]], v1 = A[r1 * ld + jc[c]];
+                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0);
+                    A[r1 * ld + jc[c]] = fma(-l1, pk[c], v1);
+                }
+            }
+        }
+        if (r < m) {
+            const double l0 = A[r * ld + k];
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+                if (c < nch && jc[c] <= m) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
+        }
+        __syncthreads();
+    }
+    if (warp != 0) return;
+    if (s_flag) {
+        for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)NAN;
+        if (a.status && lane == 0) a.status[i] = RBFSL_ESINGULAR;
+        return;
+    }
+    // ---- back substitution on the rhs column (warp 0)
+    for (int r = m - 1; r >= 0; --r) {
+        const double xr = A[r * ld + m] / A[r * ld + r];
+        __syncwarp();
+        if (lane == 0) A[r * ld + m] = xr;
+        for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)A[j * ld + m];
+    if (a.status && lane == 0) a.status[i] = RBFSL_OK;
+}
+
 int weights_layout(int n, int ell, int *m, int *ld, int *warp_doubles, int *wpb) {
     *m = n + (ell + 1) * (ell + 1);
     *ld = (*m + 1) | 1;  // odd stride: column accesses hit distinct banks
@@ -205,6 +342,20 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     a.P = p; a.status = status;
     int wpb = 1;
     const int smem = weights_layout(n, ell, &a.m, &a.ld, &a.warp_doubles, &wpb);
+    const int per_stencil = a.warp_doubles * 8;
+    if (per_stencil > 40 * 1024) {
+        // large systems: one CTA of four warps per point
+        if (w_dtype == RBFSL_F64) {
+            RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_cta_kernel<double>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, per_stencil));
+            weights_cta_kernel<double><<<(unsigned)Nq, kCtaWarps * kWarp, per_stencil, s>>>(a, (double *)w);
+        } else {
+            RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_cta_kernel<float>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, per_stencil));
+            weights_cta_kernel<float><<<(unsigned)Nq, kCtaWarps * kWarp, per_stencil, s>>>(a, (float *)w);
+        }
+        return launch_status("stencil_weights");
+    }
     const unsigned blocks = (unsigned)((Nq + wpb - 1) / wpb);
     if (w_dtype == RBFSL_F64) {
         RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_direct_kernel<double>,
