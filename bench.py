@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--accuracy-steps", type=int, default=600,
                     help="steps of the full-trajectory accuracy runs (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace"],
+                    help="run one kernel of the workload on --nq points (for profilers); no JSON")
+    ap.add_argument("--nq", type=int, default=3040)
+    ap.add_argument("--repeat", type=int, default=3)
     return ap.parse_args()
 
 
@@ -249,10 +253,43 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_case(args):
+    """One kernel of the workload, on the first --nq departure points, --repeat times."""
+    import torch
+    from paper_1804_01609_gb300 import rbfsl
+    w = workload()
+    N, n = w.N, w.n
+    nq = min(args.nq, N)
+    x = torch.as_tensor(w.X, device="cuda")
+    xi = torch.empty_like(x)
+    rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, 0.3, w.dt, rbfsl.FP64, xi)
+    ix = rbfsl.rbfsl_knn_index_create(x, n)
+    I = torch.empty((N, n), dtype=torch.int32, device="cuda")
+    rbfsl.rbfsl_knn_query(ix, xi, n, I)
+    W = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    rbfsl.rbfsl_stencil_weights(x, I, n, w.ell, rbfsl.PHS, w.power, xi, W)
+    q = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
+    qo = torch.empty_like(q)
+    torch.cuda.synchronize()
+    for _ in range(args.repeat):
+        if args.case == "weights":
+            rbfsl.rbfsl_stencil_weights(x, I[:nq], n, w.ell, rbfsl.PHS, w.power, xi[:nq], W[:nq])
+        elif args.case == "gather":
+            rbfsl.rbfsl_gather_dot(I, W, q, qo)
+        elif args.case == "knn":
+            rbfsl.rbfsl_knn_query(ix, xi[:nq], n, I[:nq])
+        else:
+            rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, 0.3, w.dt, rbfsl.MIXED, xi)
+    torch.cuda.synchronize()
+    ix.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
