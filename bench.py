@@ -3,7 +3,7 @@
 
 Workload (one "step" = one SL step of Algorithm 1: RK4 departure points, k-NN stencils,
 FP64 saddle-point weights, gather-dot W.q over all tracers): N = 40,962 Fibonacci nodes
-(1e-3 rad jitter), stencils of n = 84 nearest nodes of each departure point, PHS r^5,
+(1e-3 rad jitter), stencils of n = 84 nearest nodes of each departure point, PHS r^9,
 spherical harmonics to degree 4, reversing deformational flow psi = 2.4 y^2 cos(pi t) over
 600 steps (T_f = 1), 33 tracers (two Gaussian hills + 31 smooth random fields). Mixed
 precision = FP64 solves, FP32 tracing displacement and FP32 difference-form W.q.
@@ -244,7 +244,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^5 T=33 (sampled)",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=33 (sampled)",
                    "sample_nodes_per_step": S},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{S} node-updates per step of the workload, FP64 oracle"},
@@ -390,7 +390,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve + f32 trace/gather",
         "data": "synthetic",
-        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^5 T=33 (direct stencils)",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=33 (direct stencils)",
                    "N": N, "n": n, "ell": w.ell, "phs_power": w.power, "tracers": T,
                    "precision": "mixed", "l2": "flushed between timed steps (256 MB write)"},
         "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),

@@ -54,51 +54,65 @@ struct WeightsArgs {
     const int32_t *idx;
     int64_t Nq;
     int n, ell, half, m, ld;
-    int warp_doubles;
+    int stencil_doubles;  // shared-memory doubles per point
     const double *P;
     int32_t *status;
 };
 
-template <typename WT>
-__global__ void __launch_bounds__(128) weights_direct_kernel(WeightsArgs a, WT *__restrict__ W) {
-    extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * wpb + warp;
-    if (i >= a.Nq) return;
-    const int n = a.n, m = a.m, ld = a.ld, M = m - n;
-    double *A = smem + (size_t)warp * a.warp_doubles;
-    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n;
+// Shared-memory layout of one point: A (m x ld, the augmented [A~ | b] system), the stencil
+// coordinates (3 x n), the inverse pivots (m), one flag word.
+__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + m + 1; }
 
-    // ---- stencil coordinates and the evaluation point (a failed neighbour search leaves -1)
-    bool bad = false;
-    for (int j = lane; j < n; j += kWarp) {
+// NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
+// the group barrier is __syncwarp; with NW = 4 a block is one point and uses __syncthreads.
+template <int NW, typename WT>
+__global__ void __launch_bounds__(128) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
+    extern __shared__ double smem[];
+    constexpr int GT = NW * kWarp;
+    const int g = threadIdx.x / GT, t = threadIdx.x % GT;
+    const int warp = t >> 5, lane = t & 31;
+    const int spb = blockDim.x / GT;
+    const int64_t i = (int64_t)blockIdx.x * spb + g;
+    if (i >= a.Nq) return;  // NW == 1 only (with NW > 1 the grid has exactly Nq blocks)
+    const int n = a.n, m = a.m, ld = a.ld, M = m - n;
+    double *A = smem + (size_t)g * a.stencil_doubles;
+    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n, *invp = cz + n;
+    int *flag = reinterpret_cast<int *>(invp + m);
+    auto gsync = [] {
+        if (NW == 1) __syncwarp(); else __syncthreads();
+    };
+
+    if (t == 0) *flag = 0;
+    gsync();
+    for (int j = t; j < n; j += GT) {
         const int64_t s = a.idx[i * n + j];
-        if (s < 0) { bad = true; continue; }
+        if (s < 0) { *flag = 1; continue; }  // a failed neighbour search leaves -1
         cx[j] = a.X[3 * s];
         cy[j] = a.X[3 * s + 1];
         cz[j] = a.X[3 * s + 2];
     }
-    if (__any_sync(0xffffffffu, bad)) {
-        for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)NAN;
-        if (a.status && lane == 0) a.status[i] = RBFSL_EKNN;
+    gsync();
+    if (*flag) {
+        for (int j = t; j < n; j += GT) W[i * n + j] = (WT)NAN;
+        if (a.status && t == 0) a.status[i] = RBFSL_EKNN;
         return;
     }
     const double px = a.P[3 * i], py = a.P[3 * i + 1], pz = a.P[3 * i + 2];
-    __syncwarp();
 
-    // ---- assembly: RBF block (symmetric, zero diagonal), harmonics block, zero block, rhs
-    for (int r = 0; r < n; ++r) {
-        const double xr = cx[r], yr = cy[r], zr = cz[r];
-        if (lane == 0) A[r * ld + r] = 0.0;
-        for (int c = r + 1 + lane; c < n; c += kWarp) {
-            const double dx = xr - cx[c], dy = yr - cy[c], dz = zr - cz[c];
-            const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
-            A[r * ld + c] = v;
-            A[c * ld + r] = v;
-        }
+    // ---- assembly. RBF block: the n(n-1)/2 pairs j < k are folded into rows of n-1 pairs
+    // (row f and row n-1-f together) so that every thread has work.
+    const int P2 = n * (n - 1) / 2;
+    for (int p = t; p < P2; p += GT) {
+        const int f = p / (n - 1), e = p - f * (n - 1);
+        int r, c;
+        if (e < n - 1 - f) { r = f; c = f + 1 + e; } else { r = n - 1 - f; c = e + 1; }
+        const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
+        const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
+        A[r * ld + c] = v;
+        A[c * ld + r] = v;
     }
-    for (int j = lane; j < n; j += kWarp) {
+    for (int j = t; j < n; j += GT) {
+        A[j * ld + j] = 0.0;
         sh_eval(a.ell, cx[j], cy[j], cz[j], [&](int c, double v) {
             A[j * ld + n + c] = v;
             A[(n + c) * ld + j] = v;
@@ -106,186 +120,58 @@ __global__ void __launch_bounds__(128) weights_direct_kernel(WeightsArgs a, WT *
         const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
         A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
     }
-    for (int e = lane; e < M * M; e += kWarp) A[(n + e / M) * ld + n + e % M] = 0.0;
-    if (lane == 0) sh_eval(a.ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
-    __syncwarp();
-
-    // ---- Gaussian elimination with partial pivoting on [A~ | b]
-    bool singular = false;
-    for (int k = 0; k < m; ++k) {
-        double best = -1.0;
-        int bidx = m;
-        for (int r = k + lane; r < m; r += kWarp) {
-            const double v = fabs(A[r * ld + k]);
-            if (v > best) { best = v; bidx = r; }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
-            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-        }
-        if (!(best > 0.0) || !isfinite(best)) { singular = true; break; }
-        if (bidx != k) {
-            for (int c = k + lane; c <= m; c += kWarp) {
-                const double t = A[k * ld + c];
-                A[k * ld + c] = A[bidx * ld + c];
-                A[bidx * ld + c] = t;
-            }
-            __syncwarp();
-        }
-        const double inv = 1.0 / A[k * ld + k];
-        for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
-        __syncwarp();
-        // columns k+1..m (m - k of them) in chunks of 32; the pivot row in registers
-        const int ncols = m - k;
-        double pk[5];
-        int jc[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            jc[c] = k + 1 + lane + c * kWarp;
-            pk[c] = (c * kWarp < ncols && jc[c] <= m) ? A[k * ld + jc[c]] : 0.0;
-        }
-        const int nch = (ncols + kWarp - 1) / kWarp;
-        int r = k + 1;
-        for (; r + 1 < m; r += 2) {
-            const double l0 = A[r * ld + k], l1 = A[(r + 1) * ld + k];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                if (c < nch && jc[c] <= m) {
-                    const double v0 = A[r * ld + jc[c]], v1 = A[(r + 1) * ld + jc[c]];
-                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0);
-                    A[(r + 1) * ld + jc[c]] = fma(-l1, pk[c], v1);
-                }
-            }
-        }
-        if (r < m) {
-            const double l0 = A[r * ld + k];
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                if (c < nch && jc[c] <= m) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
-        }
-        __syncwarp();
-    }
-
-    if (singular) {
-        for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)NAN;
-        if (a.status && lane == 0) a.status[i] = RBFSL_ESINGULAR;
-        return;
-    }
-    // ---- back substitution on the rhs column
-    for (int r = m - 1; r >= 0; --r) {
-        const double xr = A[r * ld + m] / A[r * ld + r];
-        __syncwarp();
-        if (lane == 0) A[r * ld + m] = xr;
-        for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
-        __syncwarp();
-    }
-    for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)A[j * ld + m];
-    if (a.status && lane == 0) a.status[i] = RBFSL_OK;
-}
-
-// Four warps per point, for systems too large to give every SM sub-partition its own warp
-// with one warp per point (m > ~70: one m x (m+1) FP64 matrix is ~40-100 KB). Each SM
-// sub-partition has its own FP64 unit, so the elimination is spread over 4 warps: warp 0
-// picks the pivot, swaps and scales the column; then all warps update the trailing rows
-// (row-cyclic over warps, lanes over columns, pivot row in registers).
-constexpr int kCtaWarps = 4;
-
-template <typename WT>
-__global__ void __launch_bounds__(kCtaWarps * 32) weights_cta_kernel(WeightsArgs a, WT *__restrict__ W) {
-    extern __shared__ double smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t i = blockIdx.x;
-    const int n = a.n, m = a.m, ld = a.ld, M = m - n;
-    double *A = smem;
-    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n;
-    __shared__ int s_flag;
-
-    if (tid == 0) s_flag = 0;
-    __syncthreads();
-    for (int j = tid; j < n; j += kCtaWarps * kWarp) {
-        const int64_t s = a.idx[i * n + j];
-        if (s < 0) { s_flag = 1; continue; }
-        cx[j] = a.X[3 * s];
-        cy[j] = a.X[3 * s + 1];
-        cz[j] = a.X[3 * s + 2];
-    }
-    __syncthreads();
-    if (s_flag) {
-        for (int j = tid; j < n; j += kCtaWarps * kWarp) W[i * n + j] = (WT)NAN;
-        if (a.status && tid == 0) a.status[i] = RBFSL_EKNN;
-        return;
-    }
-    const double px = a.P[3 * i], py = a.P[3 * i + 1], pz = a.P[3 * i + 2];
-
-    // ---- assembly
-    for (int r = warp; r < n; r += kCtaWarps) {
-        const double xr = cx[r], yr = cy[r], zr = cz[r];
-        if (lane == 0) A[r * ld + r] = 0.0;
-        for (int c = r + 1 + lane; c < n; c += kWarp) {
-            const double dx = xr - cx[c], dy = yr - cy[c], dz = zr - cz[c];
-            const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
-            A[r * ld + c] = v;
-            A[c * ld + r] = v;
-        }
-    }
-    for (int j = tid; j < n; j += kCtaWarps * kWarp) {
-        sh_eval(a.ell, cx[j], cy[j], cz[j], [&](int c, double v) {
-            A[j * ld + n + c] = v;
-            A[(n + c) * ld + j] = v;
-        });
-        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
-        A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
-    }
-    for (int e = tid; e < M * M; e += kCtaWarps * kWarp) A[(n + e / M) * ld + n + e % M] = 0.0;
-    if (tid == 0) sh_eval(a.ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
-    __syncthreads();
+    for (int e = t; e < M * M; e += GT) A[(n + e / M) * ld + n + e % M] = 0.0;
+    if (t == 0) sh_eval(a.ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
+    gsync();
 
     // ---- Gaussian elimination with partial pivoting on [A~ | b]
     for (int k = 0; k < m; ++k) {
         if (warp == 0) {
-            double best = -1.0;
+            // pivot: largest |a_rk| (integer compare of the magnitude bits), smaller row on a tie
+            long long best = -1;
             int bidx = m;
             for (int r = k + lane; r < m; r += kWarp) {
-                const double v = fabs(A[r * ld + k]);
+                const long long v = __double_as_longlong(A[r * ld + k]) & 0x7fffffffffffffffLL;
                 if (v > best) { best = v; bidx = r; }
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
                 const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
                 if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
             }
-            if (!(best > 0.0) || !isfinite(best)) {
-                if (lane == 0) s_flag = 2;
+            if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
+                if (lane == 0) *flag = 2;
             } else {
                 if (bidx != k) {
                     for (int c = k + lane; c <= m; c += kWarp) {
-                        const double t = A[k * ld + c];
+                        const double tmp = A[k * ld + c];
                         A[k * ld + c] = A[bidx * ld + c];
-                        A[bidx * ld + c] = t;
+                        A[bidx * ld + c] = tmp;
                     }
                     __syncwarp();
                 }
                 const double inv = 1.0 / A[k * ld + k];
+                if (lane == 0) invp[k] = inv;
                 for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
             }
         }
-        __syncthreads();
-        if (s_flag) break;
+        gsync();
+        if (*flag) break;
+        // trailing update: rows k+1.. cyclic over the NW warps (two at a time), lanes over the
+        // m - k columns k+1..m in chunks of 32 with the pivot row held in registers
         const int ncols = m - k;
+        const int nch = (ncols + kWarp - 1) / kWarp;
         double pk[5];
         int jc[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             jc[c] = k + 1 + lane + c * kWarp;
-            pk[c] = (c * kWarp < ncols && jc[c] <= m) ? A[k * ld + jc[c]] : 0.0;
+            pk[c] = jc[c] <= m ? A[k * ld + jc[c]] : 0.0;
         }
-        const int nch = (ncols + kWarp - 1) / kWarp;
         int r = k + 1 + warp;
-        for (; r + kCtaWarps < m; r += 2 * kCtaWarps) {
-            const int r1 = r + kCtaWarps;
+        for (; r + NW < m; r += 2 * NW) {
+            const int r1 = r + NW;
             const double l0 = A[r * ld + k], l1 = A[r1 * ld + k];
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
@@ -302,17 +188,17 @@ __global__ void __launch_bounds__(kCtaWarps * 32) weights_cta_kernel(WeightsArgs
             for (int c = 0; c < 5; ++c)
                 if (c < nch && jc[c] <= m) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
         }
-        __syncthreads();
+        gsync();
     }
     if (warp != 0) return;
-    if (s_flag) {
+    if (*flag) {
         for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)NAN;
         if (a.status && lane == 0) a.status[i] = RBFSL_ESINGULAR;
         return;
     }
-    // ---- back substitution on the rhs column (warp 0)
+    // ---- back substitution on the rhs column (warp 0), with the stored inverse pivots
     for (int r = m - 1; r >= 0; --r) {
-        const double xr = A[r * ld + m] / A[r * ld + r];
+        const double xr = A[r * ld + m] * invp[r];
         __syncwarp();
         if (lane == 0) A[r * ld + m] = xr;
         for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
@@ -322,14 +208,14 @@ __global__ void __launch_bounds__(kCtaWarps * 32) weights_cta_kernel(WeightsArgs
     if (a.status && lane == 0) a.status[i] = RBFSL_OK;
 }
 
-int weights_layout(int n, int ell, int *m, int *ld, int *warp_doubles, int *wpb) {
-    *m = n + (ell + 1) * (ell + 1);
-    *ld = (*m + 1) | 1;  // odd stride: column accesses hit distinct banks
-    *warp_doubles = *m * *ld + 3 * n;
-    const int per_warp = *warp_doubles * 8;
-    *wpb = 100 * 1024 / per_warp;
-    *wpb = *wpb < 1 ? 1 : (*wpb > 4 ? 4 : *wpb);
-    return per_warp * *wpb;
+template <int NW, typename WT>
+int launch_weights_nw(const WeightsArgs &a, int spb, void *w, cudaStream_t s) {
+    const int smem = spb * a.stencil_doubles * 8;
+    RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_kernel<NW, WT>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const unsigned blocks = (unsigned)((a.Nq + spb - 1) / spb);
+    weights_kernel<NW, WT><<<blocks, spb * NW * kWarp, smem, s>>>(a, (WT *)w);
+    return launch_status("stencil_weights");
 }
 
 int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int ell, int power,
@@ -340,33 +226,19 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     WeightsArgs a{};
     a.X = x; a.idx = idx; a.Nq = Nq; a.n = n; a.ell = ell; a.half = (power - 1) / 2;
     a.P = p; a.status = status;
-    int wpb = 1;
-    const int smem = weights_layout(n, ell, &a.m, &a.ld, &a.warp_doubles, &wpb);
-    const int per_stencil = a.warp_doubles * 8;
-    if (per_stencil > 40 * 1024) {
-        // large systems: one CTA of four warps per point
-        if (w_dtype == RBFSL_F64) {
-            RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_cta_kernel<double>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, per_stencil));
-            weights_cta_kernel<double><<<(unsigned)Nq, kCtaWarps * kWarp, per_stencil, s>>>(a, (double *)w);
-        } else {
-            RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_cta_kernel<float>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, per_stencil));
-            weights_cta_kernel<float><<<(unsigned)Nq, kCtaWarps * kWarp, per_stencil, s>>>(a, (float *)w);
-        }
-        return launch_status("stencil_weights");
+    a.m = n + (ell + 1) * (ell + 1);
+    a.ld = (a.m + 1) | 1;  // odd stride: column accesses hit distinct banks
+    a.stencil_doubles = stencil_doubles(n, a.m, a.ld);
+    const int bytes = a.stencil_doubles * 8;
+    if (bytes > 40 * 1024) {
+        // large systems (m >~ 70): four warps per point so that every SM sub-partition's FP64
+        // unit is fed although only one or two points fit in shared memory
+        return w_dtype == RBFSL_F64 ? launch_weights_nw<4, double>(a, 1, w, s)
+                                    : launch_weights_nw<4, float>(a, 1, w, s);
     }
-    const unsigned blocks = (unsigned)((Nq + wpb - 1) / wpb);
-    if (w_dtype == RBFSL_F64) {
-        RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_direct_kernel<double>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        weights_direct_kernel<double><<<blocks, wpb * kWarp, smem, s>>>(a, (double *)w);
-    } else {
-        RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_direct_kernel<float>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        weights_direct_kernel<float><<<blocks, wpb * kWarp, smem, s>>>(a, (float *)w);
-    }
-    return launch_status("stencil_weights");
+    const int spb = 4;  // four independent points (warps) per block
+    return w_dtype == RBFSL_F64 ? launch_weights_nw<1, double>(a, spb, w, s)
+                                : launch_weights_nw<1, float>(a, spb, w, s);
 }
 
 }  // namespace rbfsl
