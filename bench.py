@@ -271,6 +271,8 @@ def run_case(args):
     q = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
     qo = torch.empty_like(q)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
     for _ in range(args.repeat):
         if args.case == "weights":
             rbfsl.rbfsl_stencil_weights(x, I[:nq], n, w.ell, rbfsl.PHS, w.power, xi[:nq], W[:nq])
@@ -280,7 +282,14 @@ def run_case(args):
             rbfsl.rbfsl_knn_query(ix, xi[:nq], n, I[:nq])
         else:
             rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, 0.3, w.dt, rbfsl.MIXED, xi)
+    e1.record()
     torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.repeat
+    extra = ""
+    if args.case == "weights":
+        m = n + (w.ell + 1) ** 2
+        extra = f" {nq * weights_flops(m) / ms / 1e9:.3f} TFLOP/s ({nq} points, m={m})"
+    print(f"case {args.case}: {ms:.3f} ms per launch{extra}", flush=True)
     ix.close()
 
 

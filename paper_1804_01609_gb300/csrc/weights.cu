@@ -169,16 +169,47 @@ __global__ void __launch_bounds__(128) weights_kernel(WeightsArgs a, WT *__restr
             jc[c] = k + 1 + lane + c * kWarp;
             pk[c] = jc[c] <= m ? A[k * ld + jc[c]] : 0.0;
         }
+        // Rows are processed two at a time; the next pair's operands are loaded before the
+        // current pair is stored, so shared-memory latency overlaps the DFMAs.
         int r = k + 1 + warp;
-        for (; r + NW < m; r += 2 * NW) {
-            const int r1 = r + NW;
-            const double l0 = A[r * ld + k], l1 = A[r1 * ld + k];
+        if (r + NW < m) {
+            double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
+            double v0[5], v1[5];
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
-                if (c < nch && jc[c] <= m) {
-                    const double v0 = A[r * ld + jc[c]], v1 = A[r1 * ld + jc[c]];
-                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0);
-                    A[r1 * ld + jc[c]] = fma(-l1, pk[c], v1);
+                const bool on = c < nch && jc[c] <= m;
+                v0[c] = on ? A[r * ld + jc[c]] : 0.0;
+                v1[c] = on ? A[(r + NW) * ld + jc[c]] : 0.0;
+            }
+            for (;;) {
+                const int rn = r + 2 * NW;
+                const bool more = rn + NW < m;
+                double nl0 = 0.0, nl1 = 0.0, nv0[5], nv1[5];
+                if (more) {
+                    nl0 = A[rn * ld + k];
+                    nl1 = A[(rn + NW) * ld + k];
+                }
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    const bool on = more && c < nch && jc[c] <= m;
+                    nv0[c] = on ? A[rn * ld + jc[c]] : 0.0;
+                    nv1[c] = on ? A[(rn + NW) * ld + jc[c]] : 0.0;
+                }
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    if (c < nch && jc[c] <= m) {
+                        A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
+                        A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
+                    }
+                }
+                r = rn;
+                if (!more) break;
+                l0 = nl0;
+                l1 = nl1;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    v0[c] = nv0[c];
+                    v1[c] = nv1[c];
                 }
             }
         }
