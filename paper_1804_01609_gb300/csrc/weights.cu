@@ -63,6 +63,71 @@ struct WeightsArgs {
 // coordinates (3 x n), the inverse pivots (m), one flag word.
 __host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + m + 1; }
 
+// Trailing update of one elimination step for the rows r0, r0 + NW, r0 + 2 NW, ... < m:
+// A[r][j] -= A[r][k] * A[k][j] for the NCH column chunks j = k+1+lane+32c <= m. NCH is a
+// compile-time count so that no FP64 instruction is issued for a chunk with no live column
+// (a predicated-off DFMA still takes an FP64 issue slot). Rows go two at a time, and the next
+// pair's operands are loaded before the current pair is stored, so shared-memory latency
+// overlaps the DFMAs.
+template <int NW, int NCH>
+__device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, int m, int k,
+                                                int r, int lane) {
+    double pk[NCH];
+    int jc[NCH];
+    bool on[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        jc[c] = k + 1 + lane + c * kWarp;
+        on[c] = jc[c] <= m;
+        pk[c] = on[c] ? A[k * ld + jc[c]] : 0.0;
+    }
+    if (r + NW < m) {
+        double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
+        double v0[NCH], v1[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            v0[c] = on[c] ? A[r * ld + jc[c]] : 0.0;
+            v1[c] = on[c] ? A[(r + NW) * ld + jc[c]] : 0.0;
+        }
+        for (;;) {
+            const int rn = r + 2 * NW;
+            const bool more = rn + NW < m;
+            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
+            if (more) {
+                nl0 = A[rn * ld + k];
+                nl1 = A[(rn + NW) * ld + k];
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                nv0[c] = (more && on[c]) ? A[rn * ld + jc[c]] : 0.0;
+                nv1[c] = (more && on[c]) ? A[(rn + NW) * ld + jc[c]] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                if (c < NCH - 1 || on[c]) {
+                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
+                    A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
+                }
+            }
+            r = rn;
+            if (!more) break;
+            l0 = nl0;
+            l1 = nl1;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                v0[c] = nv0[c];
+                v1[c] = nv1[c];
+            }
+        }
+    }
+    if (r < m) {
+        const double l0 = A[r * ld + k];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
+    }
+}
+
 // NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW = 4 a block is one point and uses __syncthreads.
 template <int NW, typename WT>
@@ -158,66 +223,14 @@ __global__ void __launch_bounds__(128) weights_kernel(WeightsArgs a, WT *__restr
         }
         gsync();
         if (*flag) break;
-        // trailing update: rows k+1.. cyclic over the NW warps (two at a time), lanes over the
-        // m - k columns k+1..m in chunks of 32 with the pivot row held in registers
-        const int ncols = m - k;
-        const int nch = (ncols + kWarp - 1) / kWarp;
-        double pk[5];
-        int jc[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-            jc[c] = k + 1 + lane + c * kWarp;
-            pk[c] = jc[c] <= m ? A[k * ld + jc[c]] : 0.0;
-        }
-        // Rows are processed two at a time; the next pair's operands are loaded before the
-        // current pair is stored, so shared-memory latency overlaps the DFMAs.
-        int r = k + 1 + warp;
-        if (r + NW < m) {
-            double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
-            double v0[5], v1[5];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const bool on = c < nch && jc[c] <= m;
-                v0[c] = on ? A[r * ld + jc[c]] : 0.0;
-                v1[c] = on ? A[(r + NW) * ld + jc[c]] : 0.0;
-            }
-            for (;;) {
-                const int rn = r + 2 * NW;
-                const bool more = rn + NW < m;
-                double nl0 = 0.0, nl1 = 0.0, nv0[5], nv1[5];
-                if (more) {
-                    nl0 = A[rn * ld + k];
-                    nl1 = A[(rn + NW) * ld + k];
-                }
-#pragma unroll
-                for (int c = 0; c < 5; ++c) {
-                    const bool on = more && c < nch && jc[c] <= m;
-                    nv0[c] = on ? A[rn * ld + jc[c]] : 0.0;
-                    nv1[c] = on ? A[(rn + NW) * ld + jc[c]] : 0.0;
-                }
-#pragma unroll
-                for (int c = 0; c < 5; ++c) {
-                    if (c < nch && jc[c] <= m) {
-                        A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
-                        A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
-                    }
-                }
-                r = rn;
-                if (!more) break;
-                l0 = nl0;
-                l1 = nl1;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) {
-                    v0[c] = nv0[c];
-                    v1[c] = nv1[c];
-                }
-            }
-        }
-        if (r < m) {
-            const double l0 = A[r * ld + k];
-#pragma unroll
-            for (int c = 0; c < 5; ++c)
-                if (c < nch && jc[c] <= m) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
+        // trailing update: rows k+1.. cyclic over the NW warps, lanes over the m - k columns
+        // k+1..m in chunks of 32 (pivot row in registers)
+        switch ((m - k + kWarp - 1) / kWarp) {
+            case 1: trailing_update<NW, 1>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 2: trailing_update<NW, 2>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 3: trailing_update<NW, 3>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 4: trailing_update<NW, 4>(A, ld, m, k, k + 1 + warp, lane); break;
+            default: trailing_update<NW, 5>(A, ld, m, k, k + 1 + warp, lane); break;
         }
         gsync();
     }
