@@ -134,6 +134,32 @@ int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *idx, int64_
 int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q,
                      int T, int dtype, void *q_out, void *stream);
 
+/* Global RBF interpolation matrix (Sec. 2.1, Eq. rbf_linsys), factorised once (Sec. 3.3):
+ * A_X[i][j] = phi(|x_i - x_j|) with phi the Gaussian exp(-(eps r)^2) (RBFSL_GAUSS) or the
+ * inverse multiquadric (1 + (eps r)^2)^(-1/2) (RBFSL_IMQ), then LU with partial pivoting
+ * (FP64, row-major). The paper factorises its positive-definite IMQ matrix by Cholesky; LU is
+ * used for every kernel because FP64 Cholesky breaks down on numerically semi-definite
+ * Gaussian matrices (eps = 6, N = 10,242).
+ *   x: device N x 3. LU: device N x N doubles, overwritten with the factors. perm: device N
+ *   int32, the row order P of P A = L U. Allocates and frees O(N) device scratch, synchronises
+ *   `stream`. Errors: EINVAL, ENOMEM, ESINGULAR (a zero pivot), ECUDA. */
+int rbfsl_global_factor(const double *x, int64_t N, int kernel, double eps, double *LU,
+                        int32_t *perm, void *stream);
+
+/* Coefficients of the global interpolant for T fields: solve A_X c = q with the factor of
+ * rbfsl_global_factor (forward and backward substitution, FP64). q, c: device N x T, may not
+ * alias. Errors: EINVAL, ECUDA. */
+int rbfsl_global_solve(const double *LU, const int32_t *perm, int64_t N, const double *q, int T,
+                       double *c, void *stream);
+
+/* Evaluate the global interpolant (Eq. srbfinterp) at Nq points for T fields:
+ *   out[i][t] = sum_j phi(|p_i - x_j|) c[j][t].
+ * dtype RBFSL_F64: c and out FP64, FP64 arithmetic. RBFSL_F32: c and out FP32, FP32 kernel
+ * values and FP32 accumulation (the mixed-precision evaluation).
+ * p: device Nq x 3, x: device N x 3. Errors: EINVAL, ECUDA. */
+int rbfsl_global_eval(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
+                      double eps, const void *c, int T, int dtype, void *out, void *stream);
+
 /* ================================================================== context (Algorithm 1) */
 typedef struct rbfsl_ctx rbfsl_ctx;
 

@@ -72,6 +72,11 @@ struct rbfsl_ctx {
     int32_t *I = nullptr, *K = nullptr, *Ik = nullptr, *status = nullptr;
     void *W = nullptr;
     unsigned long long *ctr = nullptr;  // [singular, knn failures]
+    // prepared state (global method)
+    double *LU = nullptr, *C64 = nullptr, *Q64 = nullptr;
+    float *C32 = nullptr;
+    int32_t *perm = nullptr, *piv = nullptr;
+    int prepared_T = 0;
     size_t bytes = 0;
 };
 
@@ -120,6 +125,8 @@ void release_prepared(rbfsl_ctx *c) {
     cudaFree(c->xi); cudaFree(c->I); cudaFree(c->K); cudaFree(c->Ik); cudaFree(c->status);
     cudaFree(c->W); cudaFree(c->ctr);
     c->xi = nullptr; c->I = c->K = c->Ik = c->status = nullptr; c->W = nullptr; c->ctr = nullptr;
+    cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->C32); cudaFree(c->perm); cudaFree(c->piv);
+    c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
     c->prepared = false;
 }
 
@@ -139,14 +146,63 @@ int effective_ell(const rbfsl_ctx *c) {
     return (int)std::floor(0.5 * (std::sqrt((double)c->n) - 1.0));
 }
 
+// Global method (Sec. 3.3): A_X assembled and factorised once; per step a solve and an
+// evaluation at the departure points.
+int prepare_global(rbfsl_ctx *c) {
+    if (c->kkind != RBFSL_GAUSS && c->kkind != RBFSL_IMQ)
+        return fail(c, RBFSL_EINVAL, "the global method needs RBFSL_GAUSS or RBFSL_IMQ");
+    const int64_t N = c->N, T = c->T;
+    int rc;
+    if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->LU, N * N * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->perm, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->piv, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->status, sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->C64, N * T * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->ctr, 2 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 2 * sizeof(unsigned long long), c->stream));
+    if (c->precision == RBFSL_MIXED) {
+        if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
+        if ((rc = dalloc(c, &c->C32, N * T * sizeof(float)))) return rc;
+    }
+    CTX_RC(c, global_factor_full(c->X, N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
+    c->prepared_T = c->T;
+    c->prepared = true;
+    return RBFSL_OK;
+}
+
+int one_step_global(rbfsl_ctx *c) {
+    const int64_t N = c->N, NT = N * (int64_t)c->T;
+    const double t1 = c->t + c->dt;
+    const unsigned blocks = (unsigned)((NT + 255) / 256);
+    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    if (c->precision == RBFSL_FP64) {
+        CTX_RC(c, global_solve(c->LU, c->perm, N, (const double *)c->q, c->T, c->C64, c->stream));
+        CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T, RBFSL_F64,
+                                     c->q_next, RBFSL_F64, c->stream));
+    } else {
+        // FP64 solve of the FP32 field, FP32 evaluation
+        convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q, c->Q64, NT);
+        CTX_RC(c, global_solve(c->LU, c->perm, N, c->Q64, c->T, c->C64, c->stream));
+        convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>(c->C64, c->C32, NT);
+        CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C32, c->T, RBFSL_F32,
+                                     c->q_next, RBFSL_F32, c->stream));
+    }
+    std::swap(c->q, c->q_next);
+    c->t = t1;
+    ++c->steps_done;
+    return RBFSL_OK;
+}
+
 int prepare(rbfsl_ctx *c) {
     if (c->prepared) return RBFSL_OK;
     if (!c->X) return fail(c, RBFSL_ENOTCONF, "set_nodes has not been called");
     if (c->vel_kind < 0) return fail(c, RBFSL_ENOTCONF, "set_velocity has not been called");
     if (!(c->dt > 0)) return fail(c, RBFSL_ENOTCONF, "set_dt has not been called");
     if (!c->q) return fail(c, RBFSL_ENOTCONF, "set_tracers has not been called");
+    if (c->method == RBFSL_GLOBAL) return prepare_global(c);
     if (c->method != RBFSL_LOCAL)
-        return fail(c, RBFSL_EINVAL, "only the local method is available in this build");
+        return fail(c, RBFSL_EINVAL, "the RBF-PU method is not available in this build");
     if (c->n < 1 || c->n > c->N) return fail(c, RBFSL_ENOTCONF, "stencil size not set or > N");
     const int ell = effective_ell(c);
     if (ell > RBFSL_MAX_SH_DEGREE || c->n + (ell + 1) * (ell + 1) > RBFSL_MAX_SYSTEM)
@@ -175,6 +231,7 @@ int prepare(rbfsl_ctx *c) {
 }
 
 int one_step(rbfsl_ctx *c) {
+    if (c->method == RBFSL_GLOBAL) return one_step_global(c);
     const int64_t N = c->N;
     const int n = c->n, ell = effective_ell(c), pw = (int)c->kparam;
     const double t1 = c->t + c->dt;
@@ -353,6 +410,7 @@ int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, 
     const int64_t cnt = N * (int64_t)T;
     if (T != c->T || !c->q) {
         CTX_TRY(c, cudaStreamSynchronize(c->stream));
+        if (c->method == RBFSL_GLOBAL) release_prepared(c);  // per-field buffers depend on T
         cudaFree(c->q); cudaFree(c->q_next);
         c->q = c->q_next = nullptr;
         int rc;

@@ -1,0 +1,456 @@
+// Global RBF interpolation (Sec. 2.1, Eqs. srbfinterp and rbf_linsys; Sec. 3.3): the dense
+// N x N interpolation matrix A_X is factorised once (LU with partial pivoting, FP64), then
+// every step solves A_X C = Q for all tracers and evaluates the interpolant at the departure
+// points.
+//
+// Storage is row-major FP64. The factorisation is blocked right-looking LU: per panel of 64
+// columns, a column-by-column pivot/scale/update, the row swaps applied to the rest of the
+// matrix, a unit-lower triangular solve for the panel's block row, and an FP64 tiled GEMM for
+// the trailing matrix. The per-step solve uses the same GEMM on 64-row blocks of the
+// triangular factors. All of it is bound by GB300's FP64 rate.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfsl {
+
+constexpr int kNb = 64;  // panel / block size
+
+__device__ __forceinline__ double radial(int kind, double eps2, double d2) {
+    return kind == RBFSL_GAUSS ? exp(-eps2 * d2) : rsqrt(1.0 + eps2 * d2);
+}
+
+__global__ void global_assemble(const double *__restrict__ X, int64_t N, int kind, double eps2,
+                                double *__restrict__ A) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int64_t i = e / N, j = e - i * N;
+    const double dx = X[3 * i] - X[3 * j], dy = X[3 * i + 1] - X[3 * j + 1], dz = X[3 * i + 2] - X[3 * j + 2];
+    A[e] = radial(kind, eps2, dx * dx + dy * dy + dz * dz);
+}
+
+// Pivot of column j (rows j..N-1), swap rows j and p inside the panel [j0, j0 + nb), scale the
+// column below the diagonal. One block. status[0] is set on a zero / non-finite pivot.
+__global__ void __launch_bounds__(1024) lu_pivot_scale(double *__restrict__ A, int64_t N, int64_t j,
+                                                       int64_t j0, int nb, int32_t *__restrict__ piv,
+                                                       int32_t *__restrict__ status) {
+    __shared__ long long s_best[32];
+    __shared__ int s_idx[32];
+    __shared__ int s_p;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    long long best = -1;
+    int bidx = (int)N;
+    for (int64_t i = j + t; i < N; i += blockDim.x) {
+        const long long v = __double_as_longlong(A[i * N + j]) & 0x7fffffffffffffffLL;
+        if (v > best) { best = v; bidx = (int)i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+        if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (lane == 0) { s_best[warp] = best; s_idx[warp] = bidx; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        best = lane < nw ? s_best[lane] : -1;
+        bidx = lane < nw ? s_idx[lane] : (int)N;
+        for (int off = 16; off > 0; off >>= 1) {
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+            if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+        }
+        if (lane == 0) {
+            const bool bad = best <= 0 || best >= 0x7ff0000000000000LL;
+            if (bad) { status[0] = RBFSL_ESINGULAR; bidx = (int)j; }
+            s_p = bidx;
+            piv[j] = bidx;
+        }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    if (p != j) {
+        for (int64_t c = j0 + t; c < j0 + nb; c += blockDim.x) {
+            const double tmp = A[j * N + c];
+            A[j * N + c] = A[p * N + c];
+            A[p * N + c] = tmp;
+        }
+    }
+    __syncthreads();
+    const double d = A[j * N + j];
+    if (d == 0.0) return;
+    const double inv = 1.0 / d;
+    for (int64_t i = j + 1 + t; i < N; i += blockDim.x) A[i * N + j] *= inv;
+}
+
+// Rank-1 update of the panel's remaining columns: A[i][c] -= A[i][j] A[j][c] for i > j,
+// j < c < j0 + nb. One warp per row, lanes over the panel columns.
+__global__ void lu_panel_update(double *__restrict__ A, int64_t N, int64_t j, int64_t j0, int nb) {
+    const int64_t i = j + 1 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const double l = A[i * N + j];
+    for (int64_t c = j + 1 + lane; c < j0 + nb; c += 32) A[i * N + c] = fma(-l, A[j * N + c], A[i * N + c]);
+}
+
+// Apply the panel's swaps piv[j0 .. j0+nb) to the columns outside the panel.
+__global__ void lu_laswp(double *__restrict__ A, int64_t N, int64_t j0, int nb,
+                         const int32_t *__restrict__ piv) {
+    const int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t width = N - nb;
+    if (c0 >= width) return;
+    const int64_t c = c0 < j0 ? c0 : c0 + nb;
+    for (int64_t j = j0; j < j0 + nb && j < N; ++j) {
+        const int64_t p = piv[j];
+        if (p != j) {
+            const double tmp = A[j * N + c];
+            A[j * N + c] = A[p * N + c];
+            A[p * N + c] = tmp;
+        }
+    }
+}
+
+// U12 = L11^-1 A12 for the block row j0..j0+nb, columns >= j0 + nb (unit lower L11).
+__global__ void lu_trsm_row(double *__restrict__ A, int64_t N, int64_t j0, int nb) {
+    __shared__ double L[kNb][kNb + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
+        L[e / nb][e % nb] = A[(j0 + e / nb) * N + j0 + e % nb];
+    __syncthreads();
+    const int64_t c = j0 + nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double col[kNb];
+#pragma unroll
+    for (int r = 0; r < kNb; ++r) col[r] = r < nb ? A[(j0 + r) * N + c] : 0.0;
+#pragma unroll
+    for (int r = 1; r < kNb; ++r) {
+        double s = col[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) s = fma(-L[r][q], col[q], s);
+        col[r] = s;
+    }
+#pragma unroll
+    for (int r = 1; r < kNb; ++r)
+        if (r < nb) A[(j0 + r) * N + c] = col[r];
+}
+
+// C[M x Nc] -= A[M x K] B[K x Nc], K <= 64, row-major with leading dimensions lda/ldb/ldc.
+// 64 x 64 output tiles, 256 threads with 4 x 4 outputs each; K is staged through shared
+// memory in chunks of 32 (A transposed so that the inner-loop reads are conflict free).
+__global__ void __launch_bounds__(256) gemm_sub_f64(const double *__restrict__ Am, int64_t lda,
+                                                    const double *__restrict__ Bm, int64_t ldb,
+                                                    double *__restrict__ Cm, int64_t ldc,
+                                                    int64_t M, int64_t Nc, int K) {
+    constexpr int KC = 32;
+    __shared__ double As[KC][kNb + 1];  // As[k][row]
+    __shared__ double Bs[KC][kNb + 1];  // Bs[k][col]
+    const int64_t row0 = blockIdx.y * (int64_t)kNb, col0 = blockIdx.x * (int64_t)kNb;
+    const int t = threadIdx.x;
+    const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        __syncthreads();
+        for (int e = t; e < kNb * KC; e += 256) {
+            const int r = e / KC, k = e % KC;
+            As[k][r] = (row0 + r < M && k0 + k < K) ? Am[(row0 + r) * lda + k0 + k] : 0.0;
+            const int kk = e / kNb, c = e % kNb;
+            Bs[kk][c] = (k0 + kk < K && col0 + c < Nc) ? Bm[(k0 + kk) * ldb + col0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < KC; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { a[u] = As[k][tr + u]; b[u] = Bs[k][tc + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t r = row0 + tr + u;
+        if (r >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int64_t c = col0 + tc + v;
+            if (c < Nc) Cm[r * ldc + c] -= acc[u][v];
+        }
+    }
+}
+
+int launch_gemm_sub(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
+                    int64_t ldc, int64_t M, int64_t Nc, int K, cudaStream_t s) {
+    if (M <= 0 || Nc <= 0 || K <= 0) return RBFSL_OK;
+    dim3 grid((unsigned)((Nc + kNb - 1) / kNb), (unsigned)((M + kNb - 1) / kNb));
+    gemm_sub_f64<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, Nc, K);
+    return launch_status("gemm_sub_f64");
+}
+
+int global_factor(double *A, int64_t N, int32_t *piv, int32_t *status, cudaStream_t s) {
+    for (int64_t j0 = 0; j0 < N; j0 += kNb) {
+        const int nb = (int)std::min<int64_t>(kNb, N - j0);
+        for (int64_t j = j0; j < j0 + nb; ++j) {
+            lu_pivot_scale<<<1, 1024, 0, s>>>(A, N, j, j0, nb, piv, status);
+            if (j + 1 < j0 + nb && j + 1 < N) {
+                const int64_t rows = N - j - 1;
+                lu_panel_update<<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(A, N, j, j0, nb);
+            }
+        }
+        if (N > nb) lu_laswp<<<(unsigned)((N - nb + 255) / 256), 256, 0, s>>>(A, N, j0, nb, piv);
+        const int64_t rest = N - j0 - nb;
+        if (rest > 0) {
+            lu_trsm_row<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, N, j0, nb);
+            int rc = launch_gemm_sub(A + (j0 + nb) * N + j0, N, A + j0 * N + j0 + nb, N,
+                                     A + (j0 + nb) * N + j0 + nb, N, rest, rest, nb, s);
+            if (rc) return rc;
+        }
+        int rc = launch_status("global_factor");
+        if (rc) return rc;
+    }
+    return RBFSL_OK;
+}
+
+// ---- per-step solve C = A_X^-1 Q with the factor (row-major, T columns)
+__global__ void gather_rows(const double *__restrict__ Q, const int32_t *__restrict__ perm,
+                            int64_t N, int T, double *__restrict__ Y) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * T) return;
+    const int64_t i = e / T;
+    Y[e] = Q[(int64_t)perm[i] * T + (e - i * T)];
+}
+
+// In-place solve of the diagonal block b (rows r0..r0+nb) for all T columns: unit lower
+// (forward) or upper with stored diagonal (backward). One thread per column.
+__global__ void trsm_diag_block(const double *__restrict__ LU, int64_t N, int64_t r0, int nb,
+                                double *__restrict__ Y, int T, int upper) {
+    __shared__ double D[kNb][kNb + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
+        D[e / nb][e % nb] = LU[(r0 + e / nb) * N + r0 + e % nb];
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= T) return;
+    double y[kNb];
+#pragma unroll
+    for (int r = 0; r < kNb; ++r) y[r] = r < nb ? Y[(r0 + r) * T + c] : 0.0;
+    if (!upper) {
+#pragma unroll
+        for (int r = 1; r < kNb; ++r) {
+            double s = y[r];
+#pragma unroll
+            for (int q = 0; q < r; ++q) s = fma(-D[r][q], y[q], s);
+            y[r] = s;
+        }
+    } else {
+#pragma unroll
+        for (int r = kNb - 1; r >= 0; --r) {
+            if (r >= nb) continue;
+            double s = y[r];
+#pragma unroll
+            for (int q = r + 1; q < kNb; ++q)
+                if (q < nb) s = fma(-D[r][q], y[q], s);
+            y[r] = s / D[r][r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kNb; ++r)
+        if (r < nb) Y[(r0 + r) * T + c] = y[r];
+}
+
+int global_solve(const double *LU, const int32_t *perm, int64_t N, const double *Q, int T,
+                 double *C, cudaStream_t s) {
+    const int64_t NT = N * T;
+    gather_rows<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(Q, perm, N, T, C);
+    const unsigned tb = (unsigned)((T + 63) / 64);
+    // forward: L y = P q
+    for (int64_t r0 = 0; r0 < N; r0 += kNb) {
+        const int nb = (int)std::min<int64_t>(kNb, N - r0);
+        trsm_diag_block<<<tb, 64, 0, s>>>(LU, N, r0, nb, C, T, 0);
+        int rc = launch_gemm_sub(LU + (r0 + nb) * N + r0, N, C + r0 * T, T, C + (r0 + nb) * T, T,
+                                 N - r0 - nb, T, nb, s);
+        if (rc) return rc;
+    }
+    // backward: U c = y
+    const int64_t last = ((N - 1) / kNb) * kNb;
+    for (int64_t r0 = last; r0 >= 0; r0 -= kNb) {
+        const int nb = (int)std::min<int64_t>(kNb, N - r0);
+        trsm_diag_block<<<tb, 64, 0, s>>>(LU, N, r0, nb, C, T, 1);
+        int rc = launch_gemm_sub(LU + r0, N, C + r0 * T, T, C, T, r0, T, nb, s);
+        if (rc) return rc;
+    }
+    return launch_status("global_solve");
+}
+
+// ---- evaluation of the interpolant at Nq points: out[i][t] = sum_j phi(|p_i - x_j|) C[j][t]
+// FP64: tiles of 32 points x 64 tracers per block; the kernel values of a 32-node chunk are
+// computed once into shared memory and reused by all 64 tracers.
+template <typename R, typename O>
+__global__ void __launch_bounds__(256) global_eval_kernel(const double *__restrict__ P, int64_t Nq,
+                                                          const double *__restrict__ X, int64_t N,
+                                                          int kind, double eps2,
+                                                          const R *__restrict__ C, int T,
+                                                          O *__restrict__ out) {
+    constexpr int TP = 32, TT = 64, TK = 32;
+    __shared__ R Ph[TP][TK + 1];
+    __shared__ R Cs[TK][TT];
+    __shared__ double ps[TP][3];
+    const int t = threadIdx.x;
+    const int64_t p0 = blockIdx.x * (int64_t)TP;
+    const int t0 = blockIdx.y * TT;
+    if (t < TP * 3) {
+        const int64_t pi = p0 + t / 3;
+        ps[t / 3][t % 3] = pi < Nq ? P[3 * pi + t % 3] : 0.0;
+    }
+    // thread owns points (t/16)*2 .. +2 and tracers (t%16)*4 .. +4
+    const int pr = (t / 16) * 2, tc = (t % 16) * 4;
+    R acc[2][4] = {};
+    for (int64_t k0 = 0; k0 < N; k0 += TK) {
+        __syncthreads();
+        for (int e = t; e < TP * TK; e += 256) {
+            const int a = e / TK, b = e % TK;
+            const int64_t j = k0 + b;
+            R v = R(0);
+            if (j < N) {
+                if (sizeof(R) == 8) {
+                    const double dx = ps[a][0] - X[3 * j], dy = ps[a][1] - X[3 * j + 1], dz = ps[a][2] - X[3 * j + 2];
+                    v = (R)radial(kind, eps2, dx * dx + dy * dy + dz * dz);
+                } else {
+                    const float dx = (float)ps[a][0] - (float)X[3 * j], dy = (float)ps[a][1] - (float)X[3 * j + 1],
+                                dz = (float)ps[a][2] - (float)X[3 * j + 2];
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    v = (R)(kind == RBFSL_GAUSS ? __expf(-(float)eps2 * d2) : rsqrtf(1.0f + (float)eps2 * d2));
+                }
+            }
+            Ph[a][b] = v;
+        }
+        for (int e = t; e < TK * TT; e += 256) {
+            const int b = e / TT, c = e % TT;
+            const int64_t j = k0 + b;
+            Cs[b][c] = (j < N && t0 + c < T) ? C[j * T + t0 + c] : R(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int b = 0; b < TK; ++b) {
+            const R f0 = Ph[pr][b], f1 = Ph[pr + 1][b];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const R cv = Cs[b][tc + v];
+                acc[0][v] = fma(f0, cv, acc[0][v]);
+                acc[1][v] = fma(f1, cv, acc[1][v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t pi = p0 + pr + u;
+        if (pi >= Nq) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (t0 + tc + v < T) out[pi * T + t0 + tc + v] = (O)acc[u][v];
+    }
+}
+
+int launch_global_eval(const double *P, int64_t Nq, const double *X, int64_t N, int kind,
+                       double eps, const void *C, int T, int dtype, void *out, int out_dtype,
+                       cudaStream_t s) {
+    if (Nq == 0) return RBFSL_OK;
+    dim3 grid((unsigned)((Nq + 31) / 32), (unsigned)((T + 63) / 64));
+    const double e2 = eps * eps;
+    if (dtype == RBFSL_F64)
+        global_eval_kernel<double, double><<<grid, 256, 0, s>>>(P, Nq, X, N, kind, e2, (const double *)C, T, (double *)out);
+    else if (out_dtype == RBFSL_F32)
+        global_eval_kernel<float, float><<<grid, 256, 0, s>>>(P, Nq, X, N, kind, e2, (const float *)C, T, (float *)out);
+    else
+        global_eval_kernel<float, double><<<grid, 256, 0, s>>>(P, Nq, X, N, kind, e2, (const float *)C, T, (double *)out);
+    return launch_status("global_eval");
+}
+
+int launch_global_assemble(const double *X, int64_t N, int kind, double eps, double *A, cudaStream_t s) {
+    const int64_t NN = N * N;
+    global_assemble<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(X, N, kind, eps * eps, A);
+    return launch_status("global_assemble");
+}
+
+}  // namespace rbfsl
+
+// ---- C ABI
+namespace rbfsl {
+// Assemble and factorise; piv (N) and status (1) are device scratch; perm receives the final
+// row order. Synchronises the stream.
+int global_factor_full(const double *x, int64_t N, int kernel, double eps, double *LU, int32_t *perm,
+                       int32_t *piv, int32_t *status, cudaStream_t s) {
+    int rc = RBFSL_OK;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("global_factor: memset failed");
+        return RBFSL_ECUDA;
+    }
+    rc = launch_global_assemble(x, N, kernel, eps, LU, s);
+    if (rc == RBFSL_OK) rc = global_factor(LU, N, piv, status, s);
+    if (rc != RBFSL_OK) return rc;
+    std::vector<int32_t> hp(N);
+    int32_t hs = 0;
+    if (cudaMemcpyAsync(hp.data(), piv, N * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error(std::string("global_factor: ") + cudaGetErrorString(cudaGetLastError()));
+        return RBFSL_ECUDA;
+    }
+    // final row order: apply the swaps to the identity
+    std::vector<int32_t> order(N);
+    for (int64_t i = 0; i < N; ++i) order[i] = (int32_t)i;
+    for (int64_t j = 0; j < N; ++j) std::swap(order[j], order[hp[j]]);
+    if (cudaMemcpy(perm, order.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("global_factor: copy of the permutation failed");
+        return RBFSL_ECUDA;
+    }
+    if (hs != 0) {
+        set_error("global_factor: zero pivot (the interpolation matrix is singular)");
+        return RBFSL_ESINGULAR;
+    }
+    return RBFSL_OK;
+}
+}  // namespace rbfsl
+
+extern "C" int rbfsl_global_factor(const double *x, int64_t N, int kernel, double eps, double *LU,
+                                   int32_t *perm, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(N >= 1 && N <= 200000, "global_factor: N out of range");
+    RBFSL_CHECK_ARG(x && LU && perm, "global_factor: null pointer");
+    RBFSL_CHECK_ARG((kernel == RBFSL_GAUSS || kernel == RBFSL_IMQ) && eps > 0,
+                    "global_factor: kernel must be RBFSL_GAUSS or RBFSL_IMQ with eps > 0");
+    int32_t *piv = nullptr, *status = nullptr;
+    if (cudaMalloc(&piv, N * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&status, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(piv);
+        set_error("global_factor: out of device memory");
+        return RBFSL_ENOMEM;
+    }
+    const int rc = global_factor_full(x, N, kernel, eps, LU, perm, piv, status, (cudaStream_t)stream);
+    cudaFree(piv);
+    cudaFree(status);
+    return rc;
+}
+
+extern "C" int rbfsl_global_solve(const double *LU, const int32_t *perm, int64_t N, const double *q,
+                                  int T, double *c, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(N >= 1 && T >= 1, "global_solve: bad sizes");
+    RBFSL_CHECK_ARG(LU && perm && q && c && q != c, "global_solve: null or aliased pointer");
+    return global_solve(LU, perm, N, q, T, c, (cudaStream_t)stream);
+}
+
+extern "C" int rbfsl_global_eval(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
+                                 double eps, const void *c, int T, int dtype, void *out, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(Nq >= 0 && N >= 1 && T >= 1, "global_eval: bad sizes");
+    RBFSL_CHECK_ARG(Nq == 0 || (p && x && c && out), "global_eval: null pointer");
+    RBFSL_CHECK_ARG((kernel == RBFSL_GAUSS || kernel == RBFSL_IMQ) && eps > 0, "global_eval: bad kernel");
+    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32, "global_eval: bad dtype");
+    return launch_global_eval(p, Nq, x, N, kernel, eps, c, T, dtype, out, dtype, (cudaStream_t)stream);
+}

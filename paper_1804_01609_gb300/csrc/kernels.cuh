@@ -31,4 +31,12 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
 int launch_gather(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q, int T,
                   int dtype, void *q_out, cudaStream_t s);
 
+int global_factor_full(const double *x, int64_t N, int kernel, double eps, double *LU, int32_t *perm,
+                       int32_t *piv, int32_t *status, cudaStream_t s);
+int global_solve(const double *LU, const int32_t *perm, int64_t N, const double *Q, int T,
+                 double *C, cudaStream_t s);
+int launch_global_eval(const double *P, int64_t Nq, const double *X, int64_t N, int kind,
+                       double eps, const void *C, int T, int dtype, void *out, int out_dtype,
+                       cudaStream_t s);
+
 }  // namespace rbfsl

@@ -9,6 +9,8 @@
 // pivot search is a warp-shuffle arg-max). Lanes own columns during the rank-1 updates, so
 // the pivot row lives in registers and each update is one shared-memory load, one DFMA and
 // one store. GB300's FP64 rate is the roofline of this kernel: ~(2/3) m^3 flops per point.
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -131,7 +133,7 @@ __device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, 
 // NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW = 4 a block is one point and uses __syncthreads.
 template <int NW, typename WT>
-__global__ void __launch_bounds__(128) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
+__global__ void __launch_bounds__(NW == 8 ? 256 : 128) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
     extern __shared__ double smem[];
     constexpr int GT = NW * kWarp;
     const int g = threadIdx.x / GT, t = threadIdx.x % GT;
@@ -275,8 +277,16 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     a.stencil_doubles = stencil_doubles(n, a.m, a.ld);
     const int bytes = a.stencil_doubles * 8;
     if (bytes > 40 * 1024) {
-        // large systems (m >~ 70): four warps per point so that every SM sub-partition's FP64
-        // unit is fed although only one or two points fit in shared memory
+        // large systems (m >~ 70): several warps per point so that every SM sub-partition's
+        // FP64 unit is fed although only one or two points fit in shared memory.
+        // RBFSL_WEIGHTS_WARPS=8 selects eight warps per point (default four).
+        static const int nw = [] {
+            const char *e = getenv("RBFSL_WEIGHTS_WARPS");
+            return (e && atoi(e) == 8) ? 8 : 4;
+        }();
+        if (nw == 8)
+            return w_dtype == RBFSL_F64 ? launch_weights_nw<8, double>(a, 1, w, s)
+                                        : launch_weights_nw<8, float>(a, 1, w, s);
         return w_dtype == RBFSL_F64 ? launch_weights_nw<4, double>(a, 1, w, s)
                                     : launch_weights_nw<4, float>(a, 1, w, s);
     }

@@ -58,6 +58,9 @@ SIGNATURES = {
     "rbfsl_knn_query": (_I, [_P, _P, _I64, _I, _P, _P, _P]),
     "rbfsl_stencil_weights": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _D, _P, _P, _I, _P, _P]),
     "rbfsl_gather_dot": (_I, [_P, _P, _I64, _I, _P, _I, _I, _P, _P]),
+    "rbfsl_global_factor": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
+    "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
+    "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
     "rbfsl_create": (_I, [_P, _I, _P]),
     "rbfsl_destroy": (_I, [_P]),
     "rbfsl_set_nodes": (_I, [_P, _P, _I64, _I]),
@@ -182,6 +185,23 @@ def rbfsl_gather_dot(idx, w, q, q_out, stream=None):
     T = q.shape[1] if q.dim() == 2 else 1
     _check(load().rbfsl_gather_dot(_ptr(idx), _ptr(w), idx.shape[0], idx.shape[1], _ptr(q), T,
                                    _dtype_code(q), _ptr(q_out), _stream(stream)))
+
+
+def rbfsl_global_factor(x, kernel, eps, LU, perm, stream=None):
+    _check(load().rbfsl_global_factor(_ptr(x), x.shape[0], kernel, float(eps), _ptr(LU), _ptr(perm),
+                                      _stream(stream)))
+
+
+def rbfsl_global_solve(LU, perm, q, c, stream=None):
+    T = q.shape[1] if q.dim() == 2 else 1
+    _check(load().rbfsl_global_solve(_ptr(LU), _ptr(perm), q.shape[0], _ptr(q), T, _ptr(c),
+                                     _stream(stream)))
+
+
+def rbfsl_global_eval(p, x, kernel, eps, c, out, stream=None):
+    T = c.shape[1] if c.dim() == 2 else 1
+    _check(load().rbfsl_global_eval(_ptr(p), p.shape[0], _ptr(x), x.shape[0], kernel, float(eps),
+                                    _ptr(c), T, _dtype_code(c), _ptr(out), _stream(stream)))
 
 
 # --------------------------------------------------------------------------- context

@@ -1,0 +1,117 @@
+"""GPU parity of the global RBF path (Sec. 2.1, 3.3: A_X factorised once, per-step solve and
+evaluation) against the FP64 oracle, through the C ABI.
+
+Tolerances: the factor and solve are checked by the residual |A_X c - q| <= 1e-12 max|q|
+(backward stability of LU with partial pivoting, a property at any N); the FP64 evaluation
+agrees with the oracle's to 1e-13 of sum_j |phi_ij c_j| (the sum's own rounding scale); the
+FP32 evaluation to 2e-6 of that scale (FP32 kernel values and accumulation).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1804_01609_gb300 import inputs, rbfsl  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+EPS = 6.0
+
+
+def _t(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def _rows(X, rows, eps=EPS):
+    d2 = ((X[rows][:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    return np.exp(-(eps ** 2) * d2)
+
+
+def _factor_solve(X, Q):
+    N = X.shape[0]
+    x = _t(X)
+    LU = torch.empty((N, N), dtype=torch.float64, device=DEV)
+    perm = torch.empty(N, dtype=torch.int32, device=DEV)
+    rbfsl.rbfsl_global_factor(x, rbfsl.GAUSS, EPS, LU, perm)
+    C = torch.empty((N, Q.shape[1]), dtype=torch.float64, device=DEV)
+    rbfsl.rbfsl_global_solve(LU, perm, _t(Q), C)
+    return x, LU, perm, C.cpu().numpy()
+
+
+@pytest.mark.parametrize("N,T", [(642, 3), (2562, 64), (1000, 1), (130, 5)])
+def test_factor_solve_residual(orc, N, T):
+    X = inputs.nodes(N, 5)
+    Q = inputs.config_global_rotation(N=N, T=T).tracers(X)
+    _, _, perm, C = _factor_solve(X, Q)
+    A = orc.global_matrix(X, orc.GAUSS, EPS)
+    assert np.abs(A @ C - Q).max() <= 1e-12 * np.abs(Q).max()
+    p = perm.cpu().numpy()
+    assert sorted(p.tolist()) == list(range(N))
+    # the oracle's solve of the same system agrees to its conditioning
+    ref = orc.lu_solve(*orc.lu_factor(A), Q)
+    assert np.abs(A @ ref - Q).max() <= 1e-12 * np.abs(Q).max()
+
+
+@pytest.mark.parametrize("N,T", [(642, 3), (2562, 64), (777, 70)])
+def test_eval_parity(orc, N, T):
+    X = inputs.nodes(N, 6)
+    rng = np.random.default_rng(N)
+    C = rng.standard_normal((N, T))
+    P = inputs.random_unit_vectors(500, rng)
+    ref = orc.global_eval(P, X, C, orc.GAUSS, EPS)
+    scale = np.exp(-(EPS ** 2) * ((P[:, None, :] - X[None]) ** 2).sum(-1)) @ np.abs(C)
+    out = torch.empty((500, T), dtype=torch.float64, device=DEV)
+    rbfsl.rbfsl_global_eval(_t(P), _t(X), rbfsl.GAUSS, EPS, _t(C), out)
+    assert np.all(np.abs(out.cpu().numpy() - ref) <= 1e-13 * scale + 1e-300)
+    out32 = torch.empty((500, T), dtype=torch.float32, device=DEV)
+    rbfsl.rbfsl_global_eval(_t(P), _t(X), rbfsl.GAUSS, EPS, _t(C, torch.float32), out32)
+    assert np.all(np.abs(out32.cpu().numpy() - ref) <= 2e-6 * scale + 1e-30)
+
+
+def test_cfg3_full_size_factor_and_step(orc):
+    """BASELINE config 3 at full size: N=10242, Gaussian eps=6, 64 tracers. Residual of the
+    GPU factor on sampled rows, one evaluation checked on sampled points against the oracle."""
+    w = inputs.config_global_rotation()
+    X, Q = w.X, w.q0()
+    x, LU, perm, C = _factor_solve(X, Q)
+    rows = np.random.default_rng(1).choice(w.N, 200, replace=False)
+    R = _rows(X, rows) @ C - Q[rows]
+    assert np.abs(R).max() <= 1e-11 * np.abs(Q).max()
+    xi = torch.empty_like(x)
+    rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, w.dt, w.dt, rbfsl.FP64, xi)
+    out = torch.empty((w.N, w.T), dtype=torch.float64, device=DEV)
+    rbfsl.rbfsl_global_eval(xi, x, rbfsl.GAUSS, EPS, _t(C), out)
+    Xi = xi.cpu().numpy()
+    ref = orc.global_eval(Xi[rows], X, C, orc.GAUSS, EPS)
+    scale = np.exp(-(EPS ** 2) * ((Xi[rows][:, None, :] - X[None]) ** 2).sum(-1)) @ np.abs(C)
+    assert np.all(np.abs(out.cpu().numpy()[rows] - ref) <= 1e-13 * scale)
+
+
+def _ctx(w, precision, steps):
+    ctx = rbfsl.Context(0)
+    ctx.set_nodes(w.X)
+    ctx.set_velocity(w.vel_kind, w.vel_params)
+    ctx.set_method(rbfsl.GLOBAL, rbfsl.DIRECT)
+    ctx.set_kernel(rbfsl.GAUSS, w.eps)
+    ctx.set_precision(precision)
+    ctx.set_dt(w.dt)
+    ctx.set_tracers(w.q0() if precision == rbfsl.FP64 else w.q0().astype(np.float32))
+    ctx.step(steps)
+    q = ctx.get_q()
+    ctx.close()
+    return q
+
+
+def test_global_ctx_matches_oracle_small(orc):
+    """Whole SL steps of the global method through the context vs the oracle, N=642."""
+    w = inputs.config_global_rotation(N=642, T=4, steps=12)
+    q = _ctx(w, rbfsl.FP64, w.steps)
+    G = orc.GlobalInterpolator(w.X, orc.GAUSS, w.eps)
+    ref = w.q0()
+    for m in range(w.steps):
+        ref = G.apply(orc.trace_rk4(w.X, w.vel_kind, w.vel_params, (m + 1) * w.dt, w.dt), ref)
+    assert orc.rel_l2(q, ref) < 1e-9
+    qm = _ctx(w, rbfsl.MIXED, w.steps)
+    assert orc.rel_l2(qm, ref) < 1e-3
