@@ -137,25 +137,27 @@ __global__ void lu_trsm_row(double *__restrict__ A, int64_t N, int64_t j0, int n
 }
 
 // C[M x Nc] -= A[M x K] B[K x Nc], K <= 64, row-major with leading dimensions lda/ldb/ldc.
-// 64 x 64 output tiles, 256 threads with 4 x 4 outputs each; K is staged through shared
-// memory in chunks of 32 (A transposed so that the inner-loop reads are conflict free).
-__global__ void __launch_bounds__(256) gemm_sub_f64(const double *__restrict__ Am, int64_t lda,
-                                                    const double *__restrict__ Bm, int64_t ldb,
-                                                    double *__restrict__ Cm, int64_t ldc,
-                                                    int64_t M, int64_t Nc, int K) {
-    constexpr int KC = 32;
-    __shared__ double As[KC][kNb + 1];  // As[k][row]
-    __shared__ double Bs[KC][kNb + 1];  // Bs[k][col]
-    const int64_t row0 = blockIdx.y * (int64_t)kNb, col0 = blockIdx.x * (int64_t)kNb;
+// BM x BN output tiles, (BM/4)(BN/4) threads with 4 x 4 outputs each; K is staged through
+// shared memory in chunks of 32 (A transposed so that the inner-loop reads are conflict free).
+template <int BM, int BN>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_sub_f64(
+    const double *__restrict__ Am, int64_t lda, const double *__restrict__ Bm, int64_t ldb,
+    double *__restrict__ Cm, int64_t ldc, int64_t M, int64_t Nc, int K) {
+    constexpr int KC = 32, NT = (BM / 4) * (BN / 4);
+    __shared__ double As[KC][BM + 1];  // As[k][row]
+    __shared__ double Bs[KC][BN + 1];  // Bs[k][col]
+    const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
     const int t = threadIdx.x;
-    const int tr = (t / 16) * 4, tc = (t % 16) * 4;
+    const int tr = (t / (BN / 4)) * 4, tc = (t % (BN / 4)) * 4;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += KC) {
         __syncthreads();
-        for (int e = t; e < kNb * KC; e += 256) {
+        for (int e = t; e < BM * KC; e += NT) {
             const int r = e / KC, k = e % KC;
             As[k][r] = (row0 + r < M && k0 + k < K) ? Am[(row0 + r) * lda + k0 + k] : 0.0;
-            const int kk = e / kNb, c = e % kNb;
+        }
+        for (int e = t; e < KC * BN; e += NT) {
+            const int kk = e / BN, c = e % BN;
             Bs[kk][c] = (k0 + kk < K && col0 + c < Nc) ? Bm[(k0 + kk) * ldb + col0 + c] : 0.0;
         }
         __syncthreads();
@@ -185,8 +187,13 @@ __global__ void __launch_bounds__(256) gemm_sub_f64(const double *__restrict__ A
 int launch_gemm_sub(const double *A, int64_t lda, const double *B, int64_t ldb, double *C,
                     int64_t ldc, int64_t M, int64_t Nc, int K, cudaStream_t s) {
     if (M <= 0 || Nc <= 0 || K <= 0) return RBFSL_OK;
-    dim3 grid((unsigned)((Nc + kNb - 1) / kNb), (unsigned)((M + kNb - 1) / kNb));
-    gemm_sub_f64<<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, Nc, K);
+    if (Nc >= 1024) {  // trailing updates of the factorisation: large square tiles
+        dim3 grid((unsigned)((Nc + 63) / 64), (unsigned)((M + 63) / 64));
+        gemm_sub_f64<64, 64><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, Nc, K);
+    } else {  // few right-hand sides (the per-step solve): small tiles for enough blocks
+        dim3 grid((unsigned)((Nc + 31) / 32), (unsigned)((M + 31) / 32));
+        gemm_sub_f64<32, 32><<<grid, 64, 0, s>>>(A, lda, B, ldb, C, ldc, M, Nc, K);
+    }
     return launch_status("gemm_sub_f64");
 }
 
@@ -223,41 +230,48 @@ __global__ void gather_rows(const double *__restrict__ Q, const int32_t *__restr
     Y[e] = Q[(int64_t)perm[i] * T + (e - i * T)];
 }
 
-// In-place solve of the diagonal block b (rows r0..r0+nb) for all T columns: unit lower
-// (forward) or upper with stored diagonal (backward). One thread per column.
-__global__ void trsm_diag_block(const double *__restrict__ LU, int64_t N, int64_t r0, int nb,
-                                double *__restrict__ Y, int T, int upper) {
-    __shared__ double D[kNb][kNb + 1];
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
-        D[e / nb][e % nb] = LU[(r0 + e / nb) * N + r0 + e % nb];
+// In-place solve of the diagonal block (rows r0..r0+nb) for a tile of 64 right-hand sides:
+// unit lower (forward) or upper with stored diagonal (backward). Column-oriented
+// substitution: after row r is final, all threads update the remaining rows in parallel.
+__global__ void __launch_bounds__(256) trsm_diag_block(const double *__restrict__ LU, int64_t N,
+                                                       int64_t r0, int nb, double *__restrict__ Y,
+                                                       int T, int upper) {
+    extern __shared__ double sm[];
+    double *D = sm;                      // nb x (kNb + 1)
+    double *Ys = sm + kNb * (kNb + 1);   // nb x 64
+    const int t = threadIdx.x;
+    const int c0 = blockIdx.x * 64;
+    const int tw = min(64, T - c0);
+    for (int e = t; e < nb * nb; e += blockDim.x) D[(e / nb) * (kNb + 1) + e % nb] = LU[(r0 + e / nb) * N + r0 + e % nb];
+    for (int e = t; e < nb * 64; e += blockDim.x) {
+        const int r = e / 64, c = e % 64;
+        Ys[e] = c < tw ? Y[(r0 + r) * T + c0 + c] : 0.0;
+    }
     __syncthreads();
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= T) return;
-    double y[kNb];
-#pragma unroll
-    for (int r = 0; r < kNb; ++r) y[r] = r < nb ? Y[(r0 + r) * T + c] : 0.0;
     if (!upper) {
-#pragma unroll
-        for (int r = 1; r < kNb; ++r) {
-            double s = y[r];
-#pragma unroll
-            for (int q = 0; q < r; ++q) s = fma(-D[r][q], y[q], s);
-            y[r] = s;
+        for (int r = 0; r < nb - 1; ++r) {
+            const int rows = nb - 1 - r;
+            for (int e = t; e < rows * 64; e += blockDim.x) {
+                const int s = r + 1 + e / 64, c = e % 64;
+                Ys[s * 64 + c] = fma(-D[s * (kNb + 1) + r], Ys[r * 64 + c], Ys[s * 64 + c]);
+            }
+            __syncthreads();
         }
     } else {
-#pragma unroll
-        for (int r = kNb - 1; r >= 0; --r) {
-            if (r >= nb) continue;
-            double s = y[r];
-#pragma unroll
-            for (int q = r + 1; q < kNb; ++q)
-                if (q < nb) s = fma(-D[r][q], y[q], s);
-            y[r] = s / D[r][r];
+        for (int r = nb - 1; r >= 0; --r) {
+            if (t < 64) Ys[r * 64 + t] /= D[r * (kNb + 1) + r];
+            __syncthreads();
+            for (int e = t; e < r * 64; e += blockDim.x) {
+                const int s = e / 64, c = e % 64;
+                Ys[s * 64 + c] = fma(-D[s * (kNb + 1) + r], Ys[r * 64 + c], Ys[s * 64 + c]);
+            }
+            __syncthreads();
         }
     }
-#pragma unroll
-    for (int r = 0; r < kNb; ++r)
-        if (r < nb) Y[(r0 + r) * T + c] = y[r];
+    for (int e = t; e < nb * 64; e += blockDim.x) {
+        const int r = e / 64, c = e % 64;
+        if (c < tw) Y[(r0 + r) * T + c0 + c] = Ys[e];
+    }
 }
 
 int global_solve(const double *LU, const int32_t *perm, int64_t N, const double *Q, int T,
@@ -265,10 +279,12 @@ int global_solve(const double *LU, const int32_t *perm, int64_t N, const double 
     const int64_t NT = N * T;
     gather_rows<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(Q, perm, N, T, C);
     const unsigned tb = (unsigned)((T + 63) / 64);
+    const int smem = (kNb * (kNb + 1) + kNb * 64) * (int)sizeof(double);
+    RBFSL_CUDA_TRY(cudaFuncSetAttribute(trsm_diag_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // forward: L y = P q
     for (int64_t r0 = 0; r0 < N; r0 += kNb) {
         const int nb = (int)std::min<int64_t>(kNb, N - r0);
-        trsm_diag_block<<<tb, 64, 0, s>>>(LU, N, r0, nb, C, T, 0);
+        trsm_diag_block<<<tb, 256, smem, s>>>(LU, N, r0, nb, C, T, 0);
         int rc = launch_gemm_sub(LU + (r0 + nb) * N + r0, N, C + r0 * T, T, C + (r0 + nb) * T, T,
                                  N - r0 - nb, T, nb, s);
         if (rc) return rc;
@@ -277,7 +293,7 @@ int global_solve(const double *LU, const int32_t *perm, int64_t N, const double 
     const int64_t last = ((N - 1) / kNb) * kNb;
     for (int64_t r0 = last; r0 >= 0; r0 -= kNb) {
         const int nb = (int)std::min<int64_t>(kNb, N - r0);
-        trsm_diag_block<<<tb, 64, 0, s>>>(LU, N, r0, nb, C, T, 1);
+        trsm_diag_block<<<tb, 256, smem, s>>>(LU, N, r0, nb, C, T, 1);
         int rc = launch_gemm_sub(LU + r0, N, C + r0 * T, T, C, T, r0, T, nb, s);
         if (rc) return rc;
     }

@@ -1,8 +1,9 @@
 """GPU parity of the global RBF path (Sec. 2.1, 3.3: A_X factorised once, per-step solve and
 evaluation) against the FP64 oracle, through the C ABI.
 
-Tolerances: the factor and solve are checked by the residual |A_X c - q| <= 1e-12 max|q|
-(backward stability of LU with partial pivoting, a property at any N); the FP64 evaluation
+Tolerances: the factor and solve are checked by the residual of A_X c = q, bounded by
+10 sqrt(N) eps |A_X|_inf |c|_inf (the backward error of LU with partial pivoting, which grows
+like sqrt(N) eps |A||c| in practice; a property at any N); the FP64 evaluation
 agrees with the oracle's to 1e-13 of sum_j |phi_ij c_j| (the sum's own rounding scale); the
 FP32 evaluation to 2e-6 of that scale (FP32 kernel values and accumulation).
 """
@@ -22,6 +23,10 @@ EPS = 6.0
 
 def _t(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+def lu_residual_bound(N, a_inf, C):
+    return 10.0 * np.sqrt(N) * np.finfo(float).eps * a_inf * np.abs(C).max()
 
 
 def _rows(X, rows, eps=EPS):
@@ -46,12 +51,12 @@ def test_factor_solve_residual(orc, N, T):
     Q = inputs.config_global_rotation(N=N, T=T).tracers(X)
     _, _, perm, C = _factor_solve(X, Q)
     A = orc.global_matrix(X, orc.GAUSS, EPS)
-    assert np.abs(A @ C - Q).max() <= 1e-12 * np.abs(Q).max()
+    assert np.abs(A @ C - Q).max() <= lu_residual_bound(N, np.abs(A).sum(1).max(), C)
     p = perm.cpu().numpy()
     assert sorted(p.tolist()) == list(range(N))
     # the oracle's solve of the same system agrees to its conditioning
     ref = orc.lu_solve(*orc.lu_factor(A), Q)
-    assert np.abs(A @ ref - Q).max() <= 1e-12 * np.abs(Q).max()
+    assert np.abs(A @ ref - Q).max() <= lu_residual_bound(N, np.abs(A).sum(1).max(), ref)
 
 
 @pytest.mark.parametrize("N,T", [(642, 3), (2562, 64), (777, 70)])
@@ -77,8 +82,9 @@ def test_cfg3_full_size_factor_and_step(orc):
     X, Q = w.X, w.q0()
     x, LU, perm, C = _factor_solve(X, Q)
     rows = np.random.default_rng(1).choice(w.N, 200, replace=False)
-    R = _rows(X, rows) @ C - Q[rows]
-    assert np.abs(R).max() <= 1e-11 * np.abs(Q).max()
+    Ar = _rows(X, rows)
+    R = Ar @ C - Q[rows]
+    assert np.abs(R).max() <= lu_residual_bound(w.N, np.abs(Ar).sum(1).max(), C)
     xi = torch.empty_like(x)
     rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, w.dt, w.dt, rbfsl.FP64, xi)
     out = torch.empty((w.N, w.T), dtype=torch.float64, device=DEV)
