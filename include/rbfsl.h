@@ -160,6 +160,32 @@ int rbfsl_global_solve(const double *LU, const int32_t *perm, int64_t N, const d
 int rbfsl_global_eval(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
                       double eps, const void *c, int T, int dtype, void *out, void *stream);
 
+/* RBF partition of unity (Sec. 2.3, 3.3). Patches are the spherical caps |x - omega_l| < R
+ * around Mp given centres (the paper takes R = 2 sqrt(n / N) for ~n nodes per patch,
+ * Eq. rad_patches, and Mp = ceil(a N / n) centres, Eq. num_patches). Creation finds each
+ * patch's nodes, assembles its augmented PHS + spherical-harmonic system (Eq.
+ * rbf_poly_linsys, degree ell) and factorises it once (LU with partial pivoting, FP64).
+ *   x: device N x 3, centers: device Mp x 3 (copied). kernel must be RBFSL_PHS with odd p.
+ *   Synchronises `stream`. Errors: EINVAL (a patch with no node, or more than
+ *   RBFSL_MAX_SYSTEM - (ell+1)^2 nodes), ESINGULAR, ENOMEM, ECUDA. */
+typedef struct rbfsl_pu rbfsl_pu;
+enum { RBFSL_PU_WENDLAND = 0, RBFSL_PU_BSPLINE = 1 };
+int rbfsl_pu_create(rbfsl_pu **out, const double *x, int64_t N, const double *centers, int64_t Mp,
+                    double radius, int ell, int kernel, double kparam, void *stream);
+int rbfsl_pu_destroy(rbfsl_pu *pu);
+
+/* One RBF-PU interpolation (Eq. PU_interp) of T fields q (device N x T, FP64) to Nq points p:
+ * patch coefficients [c; d] = A~_l^-1 [q(X_l); 0] (FP64), then
+ *   out[i] = sum_l phi_l(p_i) s_l(p_i) / sum_l phi_l(p_i)   over patches containing p_i,
+ * phi_l(x) = phi(|x - omega_l| / R), phi = Wendland C2 (1-r)^4 (4r+1) (RBFSL_PU_WENDLAND) or
+ * the paper's cubic B-spline (Eq. bspline, RBFSL_PU_BSPLINE). dtype RBFSL_F64: FP64
+ * evaluation; RBFSL_F32: FP32 evaluation, out FP32. The handle keeps a coefficient buffer
+ * (reallocated when T changes), so calls on one handle must not overlap.
+ * status: device Nq or NULL (RBFSL_EUNCOVERED for a point in no patch, RBFSL_EINVAL for a
+ * point in more than 32 patches; out row NaN). Errors: EINVAL, ENOMEM, ECUDA. */
+int rbfsl_pu_apply(rbfsl_pu *pu, const double *q, int T, const double *p, int64_t Nq,
+                   int weight_kind, int dtype, void *out, int32_t *status, void *stream);
+
 /* ================================================================== context (Algorithm 1) */
 typedef struct rbfsl_ctx rbfsl_ctx;
 
@@ -188,6 +214,11 @@ int rbfsl_set_stencil_size(rbfsl_ctx *ctx, int n);
  * paper's rule ell = floor((sqrt(n) - 1) / 2). */
 int rbfsl_set_sh_degree(rbfsl_ctx *ctx, int ell);
 int rbfsl_set_kernel(rbfsl_ctx *ctx, int kind, double param);
+/* RBF-PU patches for the RBFSL_PU method: Mp centres (N x 3 doubles, host or device, copied),
+ * cap radius (<= 0: 2 sqrt(n / N) with n the stencil size, Eq. rad_patches) and weight
+ * function (RBFSL_PU_WENDLAND or RBFSL_PU_BSPLINE). */
+int rbfsl_set_pu(rbfsl_ctx *ctx, const double *centers, int64_t Mp, double radius,
+                 int weight_kind, int mem);
 int rbfsl_set_precision(rbfsl_ctx *ctx, int precision);
 int rbfsl_set_dt(rbfsl_ctx *ctx, double dt);
 int rbfsl_set_time(rbfsl_ctx *ctx, double t);

@@ -21,9 +21,11 @@ __global__ void count_status(const int32_t *__restrict__ st, int64_t N,
     const int32_t s = i < N ? st[i] : 0;
     const unsigned sing = __ballot_sync(0xffffffffu, s == RBFSL_ESINGULAR);
     const unsigned knn = __ballot_sync(0xffffffffu, s == RBFSL_EKNN);
+    const unsigned unc = __ballot_sync(0xffffffffu, s == RBFSL_EUNCOVERED || s == RBFSL_EINVAL);
     if ((threadIdx.x & 31) == 0) {
         if (sing) atomicAdd(&ctr[0], (unsigned long long)__popc(sing));
         if (knn) atomicAdd(&ctr[1], (unsigned long long)__popc(knn));
+        if (unc) atomicAdd(&ctr[2], (unsigned long long)__popc(unc));
     }
 }
 
@@ -77,6 +79,12 @@ struct rbfsl_ctx {
     float *C32 = nullptr;
     int32_t *perm = nullptr, *piv = nullptr;
     int prepared_T = 0;
+    // RBF-PU
+    double *pu_centers = nullptr;
+    int64_t pu_Mp = 0;
+    double pu_radius = 0.0;
+    int pu_wkind = RBFSL_PU_WENDLAND;
+    rbfsl_pu *pu = nullptr;
     size_t bytes = 0;
 };
 
@@ -126,6 +134,8 @@ void release_prepared(rbfsl_ctx *c) {
     cudaFree(c->W); cudaFree(c->ctr);
     c->xi = nullptr; c->I = c->K = c->Ik = c->status = nullptr; c->W = nullptr; c->ctr = nullptr;
     cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->C32); cudaFree(c->perm); cudaFree(c->piv);
+    if (c->pu) rbfsl_pu_destroy(c->pu);
+    c->pu = nullptr;
     c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
     c->prepared = false;
 }
@@ -159,8 +169,8 @@ int prepare_global(rbfsl_ctx *c) {
     if ((rc = dalloc(c, &c->piv, N * sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->status, sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->C64, N * T * sizeof(double)))) return rc;
-    if ((rc = dalloc(c, &c->ctr, 2 * sizeof(unsigned long long)))) return rc;
-    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 2 * sizeof(unsigned long long), c->stream));
+    if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
     if (c->precision == RBFSL_MIXED) {
         if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
         if ((rc = dalloc(c, &c->C32, N * T * sizeof(float)))) return rc;
@@ -194,6 +204,50 @@ int one_step_global(rbfsl_ctx *c) {
     return RBFSL_OK;
 }
 
+// RBF-PU (Sec. 3.3): patches and their LU factors once; per step the patch coefficients and
+// the blended evaluation at the departure points.
+int prepare_pu(rbfsl_ctx *c) {
+    if (!c->pu_centers) return fail(c, RBFSL_ENOTCONF, "set_pu has not been called");
+    if (c->kkind != RBFSL_PHS) return fail(c, RBFSL_EINVAL, "the RBF-PU method needs the PHS kernel");
+    const int64_t N = c->N, T = c->T;
+    double R = c->pu_radius;
+    if (!(R > 0)) {
+        if (c->n < 1) return fail(c, RBFSL_ENOTCONF, "RBF-PU radius needs a stencil size (nodes per patch)");
+        R = 2.0 * std::sqrt((double)c->n / (double)N);
+    }
+    const int ell = c->ell >= 0 ? c->ell : 3;
+    int rc;
+    if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->status, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+    if (c->precision == RBFSL_MIXED)
+        if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
+    CTX_RC(c, rbfsl_pu_create(&c->pu, c->X, N, c->pu_centers, c->pu_Mp, R, ell, c->kkind, c->kparam, c->stream));
+    c->bytes += c->pu->bytes;
+    c->prepared_T = c->T;
+    c->prepared = true;
+    return RBFSL_OK;
+}
+
+int one_step_pu(rbfsl_ctx *c) {
+    const int64_t N = c->N, NT = N * (int64_t)c->T;
+    const double t1 = c->t + c->dt;
+    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    const double *q64 = (const double *)c->q;
+    if (c->precision == RBFSL_MIXED) {
+        convert_kernel<float, double><<<(unsigned)((NT + 255) / 256), 256, 0, c->stream>>>((const float *)c->q, c->Q64, NT);
+        q64 = c->Q64;
+    }
+    CTX_RC(c, rbfsl_pu_apply(c->pu, q64, c->T, c->xi, N, c->pu_wkind,
+                             c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32, c->q_next, c->status, c->stream));
+    count_status<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->status, N, c->ctr);
+    std::swap(c->q, c->q_next);
+    c->t = t1;
+    ++c->steps_done;
+    return RBFSL_OK;
+}
+
 int prepare(rbfsl_ctx *c) {
     if (c->prepared) return RBFSL_OK;
     if (!c->X) return fail(c, RBFSL_ENOTCONF, "set_nodes has not been called");
@@ -201,8 +255,7 @@ int prepare(rbfsl_ctx *c) {
     if (!(c->dt > 0)) return fail(c, RBFSL_ENOTCONF, "set_dt has not been called");
     if (!c->q) return fail(c, RBFSL_ENOTCONF, "set_tracers has not been called");
     if (c->method == RBFSL_GLOBAL) return prepare_global(c);
-    if (c->method != RBFSL_LOCAL)
-        return fail(c, RBFSL_EINVAL, "the RBF-PU method is not available in this build");
+    if (c->method == RBFSL_PU) return prepare_pu(c);
     if (c->n < 1 || c->n > c->N) return fail(c, RBFSL_ENOTCONF, "stencil size not set or > N");
     const int ell = effective_ell(c);
     if (ell > RBFSL_MAX_SH_DEGREE || c->n + (ell + 1) * (ell + 1) > RBFSL_MAX_SYSTEM)
@@ -216,8 +269,8 @@ int prepare(rbfsl_ctx *c) {
     if ((rc = dalloc(c, &c->I, N * n * sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->status, N * sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->W, N * n * (c->precision == RBFSL_FP64 ? 8 : 4)))) return rc;
-    if ((rc = dalloc(c, &c->ctr, 2 * sizeof(unsigned long long)))) return rc;
-    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 2 * sizeof(unsigned long long), c->stream));
+    if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
     CTX_RC(c, rbfsl_knn_index_create(&c->knn, c->X, N, (int)n, c->stream));
     c->bytes += c->knn->bytes;
     if (c->mode == RBFSL_CENTER) {
@@ -232,6 +285,7 @@ int prepare(rbfsl_ctx *c) {
 
 int one_step(rbfsl_ctx *c) {
     if (c->method == RBFSL_GLOBAL) return one_step_global(c);
+    if (c->method == RBFSL_PU) return one_step_pu(c);
     const int64_t N = c->N;
     const int n = c->n, ell = effective_ell(c), pw = (int)c->kparam;
     const double t1 = c->t + c->dt;
@@ -285,7 +339,7 @@ int rbfsl_destroy(rbfsl_ctx *c) {
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
     release_prepared(c);
-    cudaFree(c->X); cudaFree(c->q); cudaFree(c->q_next);
+    cudaFree(c->X); cudaFree(c->q); cudaFree(c->q_next); cudaFree(c->pu_centers);
     delete c;
     return RBFSL_OK;
 }
@@ -371,6 +425,25 @@ int rbfsl_set_kernel(rbfsl_ctx *c, int kind, double param) {
     return RBFSL_OK;
 }
 
+int rbfsl_set_pu(rbfsl_ctx *c, const double *centers, int64_t Mp, double radius, int weight_kind, int mem) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (!centers || Mp < 1 || (mem != RBFSL_HOST && mem != RBFSL_DEVICE) ||
+        (weight_kind != RBFSL_PU_WENDLAND && weight_kind != RBFSL_PU_BSPLINE) || radius > 2.0)
+        return fail(c, RBFSL_EINVAL, "set_pu: bad arguments");
+    DeviceGuard g(c->device);
+    CTX_TRY(c, cudaStreamSynchronize(c->stream));
+    release_prepared(c);
+    cudaFree(c->pu_centers);
+    c->pu_centers = nullptr;
+    CTX_TRY(c, cudaMalloc(&c->pu_centers, Mp * 3 * sizeof(double)));
+    CTX_TRY(c, cudaMemcpy(c->pu_centers, centers, Mp * 3 * sizeof(double),
+                          mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+    c->pu_Mp = Mp;
+    c->pu_radius = radius;
+    c->pu_wkind = weight_kind;
+    return RBFSL_OK;
+}
+
 int rbfsl_set_precision(rbfsl_ctx *c, int precision) {
     if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
     if (precision != RBFSL_FP64 && precision != RBFSL_MIXED) return fail(c, RBFSL_EINVAL, "unknown precision");
@@ -410,7 +483,7 @@ int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, 
     const int64_t cnt = N * (int64_t)T;
     if (T != c->T || !c->q) {
         CTX_TRY(c, cudaStreamSynchronize(c->stream));
-        if (c->method == RBFSL_GLOBAL) release_prepared(c);  // per-field buffers depend on T
+        if (c->method != RBFSL_LOCAL) release_prepared(c);  // per-field buffers depend on T
         cudaFree(c->q); cudaFree(c->q_next);
         c->q = c->q_next = nullptr;
         int rc;
@@ -480,10 +553,11 @@ int rbfsl_get_stats(rbfsl_ctx *c, rbfsl_stats *out) {
     CTX_TRY(c, cudaStreamSynchronize(c->stream));
     std::memset(out, 0, sizeof(*out));
     if (c->ctr) {
-        unsigned long long h[2] = {0, 0};
+        unsigned long long h[3] = {0, 0, 0};
         CTX_TRY(c, cudaMemcpy(h, c->ctr, sizeof(h), cudaMemcpyDeviceToHost));
         out->singular_points = (int64_t)h[0];
         out->knn_failures = (int64_t)h[1];
+        out->uncovered_points = (int64_t)h[2];
     }
     out->steps_done = c->steps_done;
     out->time = c->t;

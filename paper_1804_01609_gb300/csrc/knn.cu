@@ -14,11 +14,6 @@
 
 namespace rbfsl {
 
-__device__ __forceinline__ int cell_coord(double v, double inv_cell, int G) {
-    int c = (int)floor((v + 1.0) * inv_cell);
-    return c < 0 ? 0 : (c >= G ? G - 1 : c);
-}
-
 __global__ void knn_cell_count(const double *__restrict__ X, int64_t N, int G, double inv_cell,
                                int32_t *__restrict__ cell_of, int32_t *__restrict__ counts) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -131,14 +126,6 @@ void knn_index_free(rbfsl_knn_index *ix) {
     ix->sid = ix->cell_start = nullptr;
 }
 
-struct KnnGrid {
-    const double *sx, *sy, *sz;
-    const int32_t *sid, *cell_start;
-    int G;
-    double inv_cell;
-    double r2_per_k;
-};
-
 __device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
     return da < db || (da == db && ia < ib);
 }
@@ -167,26 +154,16 @@ __global__ void __launch_bounds__(128) knn_query_kernel(KnnGrid g, const double 
         if (lane == 0) *cnt = 0;
         __syncwarp();
         const double rb = sqrt(r2) * (1.0 + 1e-9) + 1e-15;
-        const int x0 = cell_coord(qx - rb, g.inv_cell, g.G), x1 = cell_coord(qx + rb, g.inv_cell, g.G);
-        const int y0 = cell_coord(qy - rb, g.inv_cell, g.G), y1 = cell_coord(qy + rb, g.inv_cell, g.G);
-        const int z0 = cell_coord(qz - rb, g.inv_cell, g.G), z1 = cell_coord(qz + rb, g.inv_cell, g.G);
-        const int nx = x1 - x0 + 1, ny = y1 - y0 + 1, nz = z1 - z0 + 1;
-        const int nb = nx * ny * nz;
-        for (int t = lane; t < nb; t += kWarp) {
-            const int cx = x0 + t % nx, cy = y0 + (t / nx) % ny, cz = z0 + t / (nx * ny);
-            const int c = (cz * g.G + cy) * g.G + cx;
-            const int b = g.cell_start[c], e = g.cell_start[c + 1];
-            for (int p = b; p < e; ++p) {
-                const double d2 = sqdist_rn(qx, qy, qz, g.sx[p], g.sy[p], g.sz[p]);
-                if (d2 <= r2) {
-                    const int slot = atomicAdd(cnt, 1);
-                    if (slot < cap) {
-                        bd[slot] = d2;
-                        bi[slot] = g.sid[p];
-                    }
+        grid_ball_foreach(g, qx, qy, qz, rb, lane, [&](int p) {
+            const double d2 = sqdist_rn(qx, qy, qz, g.sx[p], g.sy[p], g.sz[p]);
+            if (d2 <= r2) {
+                const int slot = atomicAdd(cnt, 1);
+                if (slot < cap) {
+                    bd[slot] = d2;
+                    bi[slot] = g.sid[p];
                 }
             }
-        }
+        });
         __syncwarp();
         total = *cnt;
         __syncwarp();
@@ -242,7 +219,7 @@ int launch_knn(const rbfsl_knn_index *ix, const double *q, int64_t Nq, int k, in
     while (cap < 3 * k) cap <<= 1;
     const int wpb = 4;
     const size_t smem = (size_t)wpb * cap * (sizeof(double) + sizeof(int)) + wpb * sizeof(int);
-    KnnGrid g{ix->sx, ix->sy, ix->sz, ix->sid, ix->cell_start, ix->G, ix->G / 2.0, ix->r2_per_k};
+    const KnnGrid g = grid_view(ix);
     if (smem > 48 * 1024)
         RBFSL_CUDA_TRY(cudaFuncSetAttribute(knn_query_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

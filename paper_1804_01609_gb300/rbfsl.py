@@ -23,6 +23,7 @@ PHS, GAUSS, IMQ = 0, 1, 2
 FP64, MIXED = 0, 1
 F64, F32 = 0, 1
 HOST, DEVICE = 0, 1
+PU_WENDLAND, PU_BSPLINE = 0, 1
 
 _NAMES = {OK: "OK", EINVAL: "EINVAL", ENOTCONF: "ENOTCONF", ENOMEM: "ENOMEM",
           ESINGULAR: "ESINGULAR", EUNCOVERED: "EUNCOVERED", ETIMEDOUT: "ETIMEDOUT",
@@ -61,6 +62,10 @@ SIGNATURES = {
     "rbfsl_global_factor": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
+    "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
+    "rbfsl_pu_destroy": (_I, [_P]),
+    "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
+    "rbfsl_set_pu": (_I, [_P, _P, _I64, _D, _I, _I]),
     "rbfsl_create": (_I, [_P, _I, _P]),
     "rbfsl_destroy": (_I, [_P]),
     "rbfsl_set_nodes": (_I, [_P, _P, _I64, _I]),
@@ -204,6 +209,41 @@ def rbfsl_global_eval(p, x, kernel, eps, c, out, stream=None):
                                     _ptr(c), T, _dtype_code(c), _ptr(out), _stream(stream)))
 
 
+class PU:
+    """RBF-PU patches with their LU factors (rbfsl_pu_create / rbfsl_pu_destroy)."""
+
+    def __init__(self, x, centers, radius, ell, kernel, kparam, stream=None):
+        self._h = ctypes.c_void_p()
+        _check(load().rbfsl_pu_create(ctypes.byref(self._h), _ptr(x), x.shape[0], _ptr(centers),
+                                      centers.shape[0], float(radius), ell, kernel, float(kparam),
+                                      _stream(stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().rbfsl_pu_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rbfsl_pu_create(x, centers, radius, ell, kernel, kparam, stream=None) -> PU:
+    return PU(x, centers, radius, ell, kernel, kparam, stream)
+
+
+def rbfsl_pu_apply(pu, q, p, weight_kind, out, status=None, stream=None):
+    T = q.shape[1] if q.dim() == 2 else 1
+    _check(load().rbfsl_pu_apply(pu.handle, _ptr(q), T, _ptr(p), p.shape[0], weight_kind,
+                                 _dtype_code(out), _ptr(out), _ptr(status), _stream(stream)))
+
+
 # --------------------------------------------------------------------------- context
 class Context:
     """Algorithm 1 on the device: set the problem, then step. Method names follow the C ABI
@@ -253,6 +293,10 @@ class Context:
 
     def set_kernel(self, kind, param):
         self._c(load().rbfsl_set_kernel(self._h, kind, float(param)))
+
+    def set_pu(self, centers, radius=0.0, weight_kind=PU_WENDLAND):
+        c = np.ascontiguousarray(centers, dtype=np.float64)
+        self._c(load().rbfsl_set_pu(self._h, c.ctypes.data, c.shape[0], float(radius), weight_kind, HOST))
 
     def set_precision(self, prec):
         self._c(load().rbfsl_set_precision(self._h, prec))
