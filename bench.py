@@ -5,7 +5,7 @@ Workload (one "step" = one SL step of Algorithm 1: RK4 departure points, k-NN st
 FP64 saddle-point weights, gather-dot W.q over all tracers): N = 40,962 Fibonacci nodes
 (1e-3 rad jitter), stencils of n = 84 nearest nodes of each departure point, PHS r^9,
 spherical harmonics to degree 4, reversing deformational flow psi = 2.4 y^2 cos(pi t) over
-600 steps (T_f = 1), 33 tracers (two Gaussian hills + 31 smooth random fields). Mixed
+600 steps (T_f = 1), 32 tracers (one field of two Gaussian hills + 31 smooth random fields). Mixed
 precision = FP64 solves, FP32 tracing displacement and FP32 difference-form W.q.
 
 The L2 cache (129 MB) is flushed between timed steps by writing a 256 MB buffer, so every
@@ -133,11 +133,11 @@ def weights_flops(m):
     return 2.0 / 3.0 * m ** 3 + 2.0 * m ** 2
 
 
-def make_ctx(w, precision, stream, rbfsl):
+def make_ctx(w, precision, stream, rbfsl, mode=None):
     ctx = rbfsl.Context(0, stream=stream)
     ctx.set_nodes(w.X)
     ctx.set_velocity(w.vel_kind, w.vel_params)
-    ctx.set_method(rbfsl.LOCAL, rbfsl.DIRECT)
+    ctx.set_method(rbfsl.LOCAL, rbfsl.DIRECT if mode is None else mode)
     ctx.set_stencil_size(w.n)
     ctx.set_sh_degree(w.ell)
     ctx.set_kernel(rbfsl.PHS, w.power)
@@ -178,8 +178,8 @@ def time_op(fn, K, stream, flush, torch):
     return float(np.mean([a.elapsed_time(b) for a, b in ev]))
 
 
-def accuracy_run(w, precision, steps, stream, rbfsl):
-    ctx = make_ctx(w, precision, stream, rbfsl)
+def accuracy_run(w, precision, steps, stream, rbfsl, mode=None):
+    ctx = make_ctx(w, precision, stream, rbfsl, mode)
     ctx.step(steps)
     q = ctx.get_q(dtype=np.float64)
     st = ctx.get_stats()
@@ -244,7 +244,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=33 (sampled)",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=32 (sampled)",
                    "sample_nodes_per_step": S},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{S} node-updates per step of the workload, FP64 oracle"},
@@ -350,6 +350,21 @@ def main():
     ctx64.close()
     value64 = N / (float(step64_ms.mean()) / 1e3)
 
+    # the paper's centre stencils: each node's saddle-point matrix factorised once (set-up),
+    # per step one nearest-node search and two triangular solves per point
+    center = {}
+    for prec, name in ((rbfsl.MIXED, "mixed"), (rbfsl.FP64, "fp64")):
+        t0 = time.perf_counter()
+        ctxc = make_ctx(w, prec, stream, rbfsl, mode=rbfsl.CENTER)
+        ctxc.step(1)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        cms = timed_steps(ctxc, max(args.steps, 10), 2, stream, flush, torch)
+        ctxc.close()
+        center[name] = {"value": N / (float(cms.mean()) / 1e3), "ms_per_step": float(cms.mean()),
+                        "p50_ms": float(np.percentile(cms, 50)), "p99_ms": float(np.percentile(cms, 99)),
+                        "setup_s": setup_s}
+
     # ---- end to end through the public API with host buffers (pinned), per step:
     # H2D of the field, one SL step, D2H of the new field
     ctx = make_ctx(w, rbfsl.MIXED, stream, rbfsl)
@@ -384,6 +399,11 @@ def main():
         acc["mixed_l2_vs_fp64"] = rel_l2(qmx, q64)
         acc["singular_points"] = int(st64.singular_points + stmx.singular_points)
         acc["knn_failures"] = int(st64.knn_failures + stmx.knn_failures)
+        qc64, _ = accuracy_run(w, rbfsl.FP64, S, stream, rbfsl, mode=rbfsl.CENTER)
+        qcmx, _ = accuracy_run(w, rbfsl.MIXED, S, stream, rbfsl, mode=rbfsl.CENTER)
+        if S == w.steps:
+            center["fp64"]["l2_vs_exact"] = rel_l2(qc64, q0)
+            center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -399,12 +419,13 @@ def main():
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve + f32 trace/gather",
         "data": "synthetic",
-        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=33 (direct stencils)",
+        "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=32 (direct stencils)",
                    "N": N, "n": n, "ell": w.ell, "phs_power": w.power, "tracers": T,
                    "precision": "mixed", "l2": "flushed between timed steps (256 MB write)"},
         "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                             "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
+        "center_stencils": center,
         "accuracy": acc,
         "clocks": clk.summary(),
         "e2e": e2e,

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -27,17 +28,6 @@ __global__ void count_status(const int32_t *__restrict__ st, int64_t N,
         if (knn) atomicAdd(&ctr[1], (unsigned long long)__popc(knn));
         if (unc) atomicAdd(&ctr[2], (unsigned long long)__popc(unc));
     }
-}
-
-// CENTER mode: the stencil of each departure point is the stored stencil of its nearest node.
-__global__ void gather_center_stencils(const int32_t *__restrict__ K, const int32_t *__restrict__ Ik,
-                                       int64_t N, int n, int32_t *__restrict__ I) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= N * n) return;
-    const int64_t i = e / n;
-    const int j = (int)(e - i * n);
-    const int32_t k = K[i];
-    I[e] = k >= 0 ? Ik[(int64_t)k * n + j] : -1;
 }
 
 template <typename A, typename B>
@@ -274,10 +264,36 @@ int prepare(rbfsl_ctx *c) {
     CTX_RC(c, rbfsl_knn_index_create(&c->knn, c->X, N, (int)n, c->stream));
     c->bytes += c->knn->bytes;
     if (c->mode == RBFSL_CENTER) {
+        // stencil of node k: x_k and its n-1 nearest neighbours (Sec. 2.2), its saddle-point
+        // matrix factorised once (LU with partial pivoting, FP64; Sec. 3.3)
+        const int64_t m = n + (ell + 1) * (ell + 1);
         if ((rc = dalloc(c, &c->K, N * sizeof(int32_t)))) return rc;
         if ((rc = dalloc(c, &c->Ik, N * n * sizeof(int32_t)))) return rc;
-        // stencil of node k: x_k and its n-1 nearest neighbours (Sec. 2.2)
+        if ((rc = dalloc(c, &c->LU, N * m * m * sizeof(double)))) return rc;
+        if ((rc = dalloc(c, &c->perm, N * m * sizeof(int32_t)))) return rc;
         CTX_RC(c, launch_knn(c->knn, c->X, N, (int)n, c->Ik, c->status, c->stream));
+        std::vector<int64_t> ms(N + 1), lo(N);
+        for (int64_t k = 0; k <= N; ++k) ms[k] = k * n;
+        for (int64_t k = 0; k < N; ++k) lo[k] = k * m * m;
+        int64_t *d_ms = nullptr, *d_lo = nullptr;
+        int32_t *d_bad = nullptr;
+        CTX_TRY(c, cudaMalloc(&d_ms, (N + 1) * sizeof(int64_t)));
+        CTX_TRY(c, cudaMalloc(&d_lo, N * sizeof(int64_t)));
+        CTX_TRY(c, cudaMalloc(&d_bad, sizeof(int32_t)));
+        CTX_TRY(c, cudaMemcpy(d_ms, ms.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        CTX_TRY(c, cudaMemcpy(d_lo, lo.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice));
+        CTX_TRY(c, cudaMemsetAsync(d_bad, 0, sizeof(int32_t), c->stream));
+        rc = launch_stencil_factor(c->X, d_ms, c->Ik, d_lo, N, (int)n, (ell + 1) * (ell + 1), ell, pw,
+                                   c->LU, c->perm, d_bad, c->stream);
+        int32_t bad = 0;
+        if (rc == RBFSL_OK) {
+            cudaError_t e = cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) rc = ctx_cuda(c, e, "centre factorisation");
+        }
+        cudaFree(d_ms); cudaFree(d_lo); cudaFree(d_bad);
+        if (rc != RBFSL_OK) return fail(c, rc, get_error());
+        if (bad) return fail(c, RBFSL_ESINGULAR, std::to_string(bad) + " singular centre stencils");
     }
     c->prepared = true;
     return RBFSL_OK;
@@ -293,13 +309,12 @@ int one_step(rbfsl_ctx *c) {
     CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
     if (c->mode == RBFSL_DIRECT) {
         CTX_RC(c, launch_knn(c->knn, c->xi, N, n, c->I, c->status, c->stream));
+        CTX_RC(c, launch_weights(c->X, c->I, N, n, ell, pw, c->xi, c->W, wdt, c->status, c->stream));
     } else {
         CTX_RC(c, launch_knn(c->knn, c->xi, N, 1, c->K, c->status, c->stream));
-        const int64_t tot = N * n;
-        gather_center_stencils<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->K, c->Ik, N, n, c->I);
-        CTX_RC(c, launch_status("gather_center_stencils"));
+        CTX_RC(c, launch_center_weights(c->X, c->K, c->Ik, c->LU, c->perm, N, n, ell, pw, c->xi, c->I, c->W,
+                                        wdt, c->status, c->stream));
     }
-    CTX_RC(c, launch_weights(c->X, c->I, N, n, ell, pw, c->xi, c->W, wdt, c->status, c->stream));
     count_status<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->status, N, c->ctr);
     CTX_RC(c, launch_gather(c->I, c->W, N, n, c->q, c->T, wdt, c->q_next, c->stream));
     std::swap(c->q, c->q_next);

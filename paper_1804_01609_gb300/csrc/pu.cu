@@ -312,6 +312,21 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
     if (status && lane == 0) status[i] = RBFSL_OK;
 }
 
+// Factorise Mp stencil / patch systems given in CSR form (used by RBF-PU and by the local
+// method's centre stencils). Dynamic shared memory sized for the largest system.
+int launch_stencil_factor(const double *X, const int64_t *mstart, const int32_t *members,
+                          const int64_t *lu_off, int64_t count, int max_n, int M, int ell,
+                          int power, double *LU, int32_t *perm, int32_t *status, cudaStream_t s) {
+    int rc = sh_tables_init();
+    if (rc) return rc;
+    const int mmax = max_n + M;
+    const int smem = ((mmax * (mmax | 1)) + 3 * max_n) * (int)sizeof(double);
+    RBFSL_CUDA_TRY(cudaFuncSetAttribute(pu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    pu_factor_kernel<<<(unsigned)count, 128, smem, s>>>(X, mstart, members, lu_off, M, ell, (power - 1) / 2,
+                                                        LU, perm, status);
+    return launch_status("stencil_factor");
+}
+
 template <typename A, typename B>
 __global__ void pu_convert(const A *__restrict__ in, B *__restrict__ out, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -389,12 +404,9 @@ int pu_build(rbfsl_pu *u, const double *x, int64_t N, const double *centers, int
     RBFSL_CUDA_TRY(cudaMemcpyAsync(u->lu_off, lo.data(), Mp * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     RBFSL_CUDA_TRY(cudaMemsetAsync(u->status, 0, sizeof(int32_t), s));
     pu_members_kernel<<<blocks, 128, 0, s>>>(grid_view(u->nodes_ix), u->centers, Mp, R, nullptr, u->mstart, u->members);
-    const int mmax = u->max_members + u->M;
-    const int smem = ((mmax * (mmax | 1)) + 3 * u->max_members) * (int)sizeof(double);
-    RBFSL_CUDA_TRY(cudaFuncSetAttribute(pu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    pu_factor_kernel<<<(unsigned)Mp, 128, smem, s>>>(u->X, u->mstart, u->members, u->lu_off, u->M, ell,
-                                                     (power - 1) / 2, u->LU, u->perm, u->status);
-    if ((rc = launch_status("pu_build"))) return rc;
+    if ((rc = launch_stencil_factor(u->X, u->mstart, u->members, u->lu_off, Mp, u->max_members, u->M, ell,
+                                    power, u->LU, u->perm, u->status, s)))
+        return rc;
     int32_t bad = 0;
     RBFSL_CUDA_TRY(cudaMemcpyAsync(&bad, u->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RBFSL_CUDA_TRY(cudaStreamSynchronize(s));

@@ -295,6 +295,84 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
                                 : launch_weights_nw<1, float>(a, spb, w, s);
 }
 
+// Centre-stencil weights (Sec. 3.3): the departure point p_i uses the stencil of its nearest
+// node K_i, whose saddle-point matrix was factorised once (row-major LU of the m x m system,
+// row order perm). Per point: b = [phi(|p - x_Sj|); Y(p)], then L U w~ = P b with row-wise
+// dot products (lanes over a contiguous factor row, warp-shuffle sums); w = w~[0:n]. One warp
+// per point; the factor rows are streamed once, so the kernel is bound by HBM bandwidth
+// (8 m^2 bytes per point) and the FP64 rate (2 m^2 flops per point).
+template <typename WT>
+__global__ void __launch_bounds__(128) center_weights_kernel(
+    const double *__restrict__ X, const int32_t *__restrict__ Kc, const int32_t *__restrict__ Ik,
+    const double *__restrict__ LU, const int32_t *__restrict__ perm, int64_t Nq, int n, int ell,
+    int half, const double *__restrict__ P, int32_t *__restrict__ I, WT *__restrict__ W,
+    int32_t *__restrict__ status) {
+    extern __shared__ double sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int M = (ell + 1) * (ell + 1), m = n + M;
+    const int64_t i = (int64_t)blockIdx.x * 4 + warp;
+    if (i >= Nq) return;
+    double *b = sm + (size_t)warp * 2 * m, *y = b + m;
+    const int64_t k = Kc[i];
+    if (k < 0) {
+        for (int j = lane; j < n; j += 32) { W[i * n + j] = (WT)NAN; I[i * n + j] = -1; }
+        if (status && lane == 0) status[i] = RBFSL_EKNN;
+        return;
+    }
+    const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    for (int j = lane; j < n; j += 32) {
+        const int64_t s = Ik[k * n + j];
+        I[i * n + j] = (int32_t)s;
+        const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
+        b[j] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
+    }
+    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { b[n + c] = v; });
+    __syncwarp();
+    const double *F = LU + (size_t)k * m * m;
+    const int32_t *pr = perm + (size_t)k * m;
+    for (int r = lane; r < m; r += 32) y[r] = b[pr[r]];
+    __syncwarp();
+    // forward: y_r -= sum_{c<r} L_rc y_c (unit lower)
+    for (int r = 1; r < m; ++r) {
+        double s = 0.0;
+        for (int c = lane; c < r; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[r] -= s;
+        __syncwarp();
+    }
+    // backward: y_r = (y_r - sum_{c>r} U_rc y_c) / U_rr
+    for (int r = m - 1; r >= 0; --r) {
+        double s = 0.0;
+        for (int c = r + 1 + lane; c < m; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[r] = (y[r] - s) / F[(size_t)r * m + r];
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) W[i * n + j] = (WT)y[j];
+    if (status && lane == 0) status[i] = RBFSL_OK;
+}
+
+int launch_center_weights(const double *X, const int32_t *K, const int32_t *Ik, const double *LU,
+                          const int32_t *perm, int64_t Nq, int n, int ell, int power,
+                          const double *p, int32_t *I, void *w, int w_dtype, int32_t *status,
+                          cudaStream_t s) {
+    if (Nq == 0) return RBFSL_OK;
+    int rc = sh_tables_init();
+    if (rc) return rc;
+    const int m = n + (ell + 1) * (ell + 1);
+    const size_t smem = 4 * 2 * m * sizeof(double);
+    const unsigned blocks = (unsigned)((Nq + 3) / 4);
+    if (w_dtype == RBFSL_F64)
+        center_weights_kernel<double><<<blocks, 128, smem, s>>>(X, K, Ik, LU, perm, Nq, n, ell, (power - 1) / 2,
+                                                                p, I, (double *)w, status);
+    else
+        center_weights_kernel<float><<<blocks, 128, smem, s>>>(X, K, Ik, LU, perm, Nq, n, ell, (power - 1) / 2,
+                                                               p, I, (float *)w, status);
+    return launch_status("center_weights");
+}
+
 }  // namespace rbfsl
 
 extern "C" int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *idx, int64_t Nq,

@@ -209,7 +209,7 @@ def rbfsl_global_eval(p, x, kernel, eps, c, out, stream=None):
                                     _ptr(c), T, _dtype_code(c), _ptr(out), _stream(stream)))
 
 
-class PU:
+class PUPatches:
     """RBF-PU patches with their LU factors (rbfsl_pu_create / rbfsl_pu_destroy)."""
 
     def __init__(self, x, centers, radius, ell, kernel, kparam, stream=None):
@@ -234,8 +234,8 @@ class PU:
             pass
 
 
-def rbfsl_pu_create(x, centers, radius, ell, kernel, kparam, stream=None) -> PU:
-    return PU(x, centers, radius, ell, kernel, kparam, stream)
+def rbfsl_pu_create(x, centers, radius, ell, kernel, kparam, stream=None) -> PUPatches:
+    return PUPatches(x, centers, radius, ell, kernel, kparam, stream)
 
 
 def rbfsl_pu_apply(pu, q, p, weight_kind, out, status=None, stream=None):

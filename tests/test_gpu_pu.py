@@ -3,8 +3,9 @@
 Tolerances: interpolated values within 5x the oracle's own FP64 noise floor (its change when
 every node coordinate moves by one ulp) plus 1e-12 of max|q|; the invariants the method fixes
 exactly -- partition of unity, interpolation at the nodes, reproduction of spherical harmonics
-of degree <= ell -- to 1e-10; the FP32 evaluation to 1e-5 of max|q| (FP32 kernel values and
-accumulation over ~250 terms).
+of degree <= ell -- to 1e-10; the FP32 evaluation (FP32 kernel values and
+accumulation): the PHS coefficients of a patch cancel strongly (sum |c_j phi_j| is ~3e3 times
+|s| at N = 2,562 with r^7), so FP32 evaluation keeps ~3-4 digits; the bound is 2e-3 of max|q|.
 """
 import math
 
@@ -83,7 +84,7 @@ def test_pu_fp32_eval_and_uncovered():
     g64, _ = _gpu_apply(X, Om, R, q, P)
     g32, st = _gpu_apply(X, Om, R, q, P, dtype=torch.float32)
     assert (st == 0).all()
-    assert np.abs(g32 - g64).max() <= 1e-5 * np.abs(q).max()
+    assert np.abs(g32 - g64).max() <= 2e-3 * np.abs(q).max()
     # patches only on the northern hemisphere: southern points are uncovered
     keep = Om[:, 2] > 0.2
     P2 = np.array([[0.0, 0.0, -1.0], [0.0, 0.0, 1.0]])
