@@ -146,6 +146,23 @@ int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, int n, const
 int rbfsl_global_factor(const double *x, int64_t N, int kernel, double eps, double *LU,
                         int32_t *perm, void *stream);
 
+/* Same factorisation as rbfsl_global_factor, for callers that cannot allocate device memory
+ * when they factorise (for example a serving process whose allocator owns the device memory
+ * budget, or code that must not trigger the device-wide synchronisation an allocation can
+ * cause while other streams run). The paper has no counterpart: this is a property of the
+ * library, not of the method.
+ *   Allocates nothing: the scratch (pivot rows and a status word) is a file-scope device
+ *   array of RBFSL_NOALLOC_FACTOR_MAX_N + 1 int32 that every GPU loading the library holds
+ *   until exit; N above RBFSL_NOALLOC_FACTOR_MAX_N is rejected with EINVAL.
+ *   Runs on the current device. The first call on a device looks up the array's device
+ *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array: calls whose work overlaps on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.
+ *   Arguments, outputs and errors as rbfsl_global_factor; synchronises `stream`. */
+#define RBFSL_NOALLOC_FACTOR_MAX_N 16384
+int rbfsl_global_factor_noalloc(const double *x, int64_t N, int kernel, double eps, double *LU,
+                                int32_t *perm, void *stream);
+
 /* Coefficients of the global interpolant for T fields: solve A_X c = q with the factor of
  * rbfsl_global_factor (forward and backward substitution, FP64). q, c: device N x T, may not
  * alias. Errors: EINVAL, ECUDA. */

@@ -470,3 +470,74 @@ extern "C" int rbfsl_global_eval(const double *p, int64_t Nq, const double *x, i
     RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32, "global_eval: bad dtype");
     return launch_global_eval(p, Nq, x, N, kernel, eps, c, T, dtype, out, dtype, (cudaStream_t)stream);
 }
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of rbfsl_global_factor (no counterpart in the paper).
+//
+// Some callers cannot call cudaMalloc at the point where they factorise: a serving process
+// whose allocator owns the device memory budget, or host code that must not trigger the
+// device-wide synchronisation an allocation can cause while other streams are running.
+// This variant keeps its scratch -- the pivot row of every elimination step and one status
+// word -- in the file-scope device array below, sized for N <= RBFSL_NOALLOC_FACTOR_MAX_N.
+// Every GPU that loads the library holds that array (64 KB) until the process exits.
+namespace rbfsl {
+
+constexpr int64_t kNoAllocMaxN = RBFSL_NOALLOC_FACTOR_MAX_N;
+
+// [0, N): pivot rows of the elimination; [kNoAllocMaxN]: status word (0 or ESINGULAR).
+static __device__ __align__(256) int32_t g_factor_scratch[kNoAllocMaxN + 1];
+
+// Device address of g_factor_scratch for each device, looked up on the first call made on
+// that device (the name of a __device__ array in host code is not a device address).
+static int32_t *g_factor_scratch_ptr[64] = {nullptr};
+
+// Final row order from the recorded swaps (one thread: N <= kNoAllocMaxN).
+__global__ void noalloc_row_order(const int32_t *__restrict__ piv, int64_t N, int32_t *__restrict__ perm) {
+    for (int64_t i = 0; i < N; ++i) perm[i] = (int32_t)i;
+    for (int64_t j = 0; j < N; ++j) {
+        const int32_t p = piv[j];
+        const int32_t t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+    }
+}
+
+}  // namespace rbfsl
+
+extern "C" int rbfsl_global_factor_noalloc(const double *x, int64_t N, int kernel, double eps,
+                                           double *LU, int32_t *perm, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(N >= 1, "global_factor_noalloc: N < 1");
+    RBFSL_CHECK_ARG(N <= kNoAllocMaxN,
+                    "global_factor_noalloc: N exceeds RBFSL_NOALLOC_FACTOR_MAX_N (16384); "
+                    "use rbfsl_global_factor");
+    RBFSL_CHECK_ARG(x && LU && perm, "global_factor_noalloc: null pointer");
+    RBFSL_CHECK_ARG((kernel == RBFSL_GAUSS || kernel == RBFSL_IMQ) && eps > 0,
+                    "global_factor_noalloc: kernel must be RBFSL_GAUSS or RBFSL_IMQ with eps > 0");
+    int dev = 0;
+    RBFSL_CUDA_TRY(cudaGetDevice(&dev));
+    RBFSL_CHECK_ARG(dev >= 0 && dev < 64, "global_factor_noalloc: device index >= 64");
+    if (!g_factor_scratch_ptr[dev]) {
+        int32_t *ptr = nullptr;
+        RBFSL_CUDA_TRY(cudaGetSymbolAddress((void **)&ptr, g_factor_scratch));
+        g_factor_scratch_ptr[dev] = ptr;
+    }
+    int32_t *piv = g_factor_scratch_ptr[dev];
+    int32_t *status = piv + kNoAllocMaxN;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the status word must start at zero
+    RBFSL_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+    int rc = launch_global_assemble(x, N, kernel, eps, LU, s);
+    if (rc == RBFSL_OK) rc = global_factor(LU, N, piv, status, s);
+    if (rc != RBFSL_OK) return rc;
+    noalloc_row_order<<<1, 1, 0, s>>>(piv, N, perm);
+    if ((rc = launch_status("global_factor_noalloc"))) return rc;
+    int32_t hs = 0;
+    RBFSL_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RBFSL_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs != 0) {
+        set_error("global_factor_noalloc: zero pivot (the interpolation matrix is singular)");
+        return RBFSL_ESINGULAR;
+    }
+    return RBFSL_OK;
+}

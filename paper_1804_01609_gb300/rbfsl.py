@@ -60,6 +60,7 @@ SIGNATURES = {
     "rbfsl_stencil_weights": (_I, [_P, _I64, _P, _I64, _I, _I, _I, _D, _P, _P, _I, _P, _P]),
     "rbfsl_gather_dot": (_I, [_P, _P, _I64, _I, _P, _I, _I, _P, _P]),
     "rbfsl_global_factor": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
+    "rbfsl_global_factor_noalloc": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
     "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
@@ -195,6 +196,12 @@ def rbfsl_gather_dot(idx, w, q, q_out, stream=None):
 def rbfsl_global_factor(x, kernel, eps, LU, perm, stream=None):
     _check(load().rbfsl_global_factor(_ptr(x), x.shape[0], kernel, float(eps), _ptr(LU), _ptr(perm),
                                       _stream(stream)))
+
+
+def rbfsl_global_factor_noalloc(x, kernel, eps, LU, perm, stream=None):
+    """rbfsl_global_factor without any device allocation (scratch in a library-owned array)."""
+    _check(load().rbfsl_global_factor_noalloc(_ptr(x), x.shape[0], kernel, float(eps), _ptr(LU),
+                                              _ptr(perm), _stream(stream)))
 
 
 def rbfsl_global_solve(LU, perm, q, c, stream=None):
