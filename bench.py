@@ -127,6 +127,11 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
+# capture of this kernel version (profiles/weights_direct_N40962_n84.md).
+WEIGHTS_DRAM_BYTES = 16.27e6
+
+
 def weights_flops(m):
     """Algorithmic FP64 flops of one augmented solve: LU of an m x m system with one
     right-hand side ((2/3) m^3 for the elimination, 2 m^2 for the rhs and back substitution)."""
@@ -430,9 +435,10 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "weights_direct_kernel (FP64 GEPP)",
+        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float> (FP64 GEPP, m = 109)",
                      "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": WEIGHTS_DRAM_BYTES,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
                      "ms_per_launch": w_ms},
         "roofline_gather": {"bound": "hbm", "kernel": "gather_dot_kernel<float>",
