@@ -256,6 +256,49 @@ int rbfsl_get_stats(rbfsl_ctx *ctx, rbfsl_stats *out);
  * (FP64 in RBFSL_FP64 mode, FP32 in RBFSL_MIXED). NULL where the method has none. */
 int rbfsl_last_step_buffers(rbfsl_ctx *ctx, const double **xi, const int32_t **idx,
                             const void **w);
+/* ================================================================== batched problems */
+/* Many independent local RBF-SL problems advanced together (each with its own nodes, stencil
+ * size, degree, PHS power, stencil mode, precision, velocity, time step and tracers). One SL
+ * step of every active problem is three small kernels and ONE persistent fused kernel (k-NN
+ * stencil, FP64 weights, gather-dot per point; stencils and weights stay on chip), captured
+ * once as a CUDA graph and replayed per step (when `stream` is not the legacy default stream).
+ * A problem's result is bit-identical alone, in any batch, and through the context API with
+ * the same settings (the same per-point device code runs in all three). */
+typedef struct rbfsl_batch rbfsl_batch;
+typedef struct rbfsl_problem {
+    int64_t N;                /* nodes */
+    const double *nodes;      /* HOST N x 3, copied */
+    int n, ell;               /* stencil size, spherical-harmonic degree */
+    double phs_power;         /* odd PHS exponent */
+    int mode;                 /* RBFSL_DIRECT or RBFSL_CENTER */
+    int precision;            /* RBFSL_FP64 or RBFSL_MIXED */
+    int vel_kind;             /* RBFSL_VEL_* */
+    double vel_params[4];     /* as rbfsl_set_velocity (unused entries 0) */
+    double t0, dt;            /* time of q0 and time step */
+    int T;                    /* tracers, 1..256 */
+    const double *q0;         /* HOST N x T FP64, copied (rounded to FP32 in mixed precision) */
+} rbfsl_problem;
+int rbfsl_batch_create(rbfsl_batch **out, int device, void *stream);
+int rbfsl_batch_destroy(rbfsl_batch *b);
+/* Add a problem (allocates its state, builds its grid index and, in RBFSL_CENTER mode, its
+ * stencil factors; synchronises the stream). *id identifies it until rbfsl_batch_remove.
+ * Errors: EINVAL, ENOMEM, ESINGULAR, ECUDA. */
+int rbfsl_batch_add(rbfsl_batch *b, const rbfsl_problem *problem, int *id);
+/* Remove a problem and free its device memory (synchronises the stream). */
+int rbfsl_batch_remove(rbfsl_batch *b, int id);
+/* Advance every problem of the batch by nsteps SL steps (asynchronous on the stream). */
+int rbfsl_batch_step(rbfsl_batch *b, int nsteps);
+/* Current field of a problem, N x T FP64 to HOST memory (synchronises the stream). */
+int rbfsl_batch_get_q(rbfsl_batch *b, int id, double *out);
+int rbfsl_batch_problem_stats(rbfsl_batch *b, int id, rbfsl_stats *out);
+/* use_graph = 0: launch the step's kernels eagerly instead of replaying a CUDA graph. */
+int rbfsl_batch_set_graph(rbfsl_batch *b, int use_graph);
+/* Autotuner: for every RBFSL_DIRECT (n, ell) class of the batch, time the persistent kernel
+ * with one warp per point and with four warps per point and keep the faster for later steps.
+ * Fields, times and step counts are unchanged. choices (may be NULL) receives triples
+ * (n, ell, points per tile: 4 = one warp per point, 1 = four warps per point). */
+int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices);
+
 /* Message of the last failed call on this context (thread-local when ctx is NULL). */
 const char *rbfsl_last_error(const rbfsl_ctx *ctx);
 const char *rbfsl_version(void);

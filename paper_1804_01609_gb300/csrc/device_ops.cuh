@@ -1,0 +1,416 @@
+// Per-point device operations shared by the single-problem kernels and the batched
+// persistent kernel, so that a problem gives bit-identical results alone or in a batch.
+#pragma once
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace rbfsl {
+
+template <typename R>
+struct Vel {
+    int kind;
+    R p0, p1, p2, p3;  // rigid: a_x, a_y, a_z, omega; deform: kappa, pi / T_f
+    __device__ __forceinline__ void operator()(R x, R y, R z, R t, R &ux, R &uy, R &uz) const {
+        if (kind == RBFSL_VEL_RIGID) {
+            const R w0 = p3 * p0, w1 = p3 * p1, w2 = p3 * p2;
+            ux = w1 * z - w2 * y;
+            uy = w2 * x - w0 * z;
+            uz = w0 * y - w1 * x;
+        } else {
+            const R g = R(2) * p0 * y * cos(p1 * t);
+            ux = -g * z;
+            uy = R(0);
+            uz = g * x;
+        }
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void normalize3(R &x, R &y, R &z) {
+    const R inv = R(1) / sqrt(x * x + y * y + z * z);
+    x *= inv;
+    y *= inv;
+    z *= inv;
+}
+
+
+// One departure point, FP64 (Sec. 3.2, Eq. sl_ode): classical RK4 backward (h = -dt) with an
+// orthogonal projection onto S^2 of every stage point and of the result.
+__device__ __forceinline__ void rk4_point_f64(const Vel<double> &u, double x, double y, double z,
+                                              double t1, double h, double &ox, double &oy,
+                                              double &oz) {
+    double k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+    u(x, y, z, t1, k1x, k1y, k1z);
+    double sx = x + 0.5 * h * k1x, sy = y + 0.5 * h * k1y, sz = z + 0.5 * h * k1z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + 0.5 * h, k2x, k2y, k2z);
+    sx = x + 0.5 * h * k2x; sy = y + 0.5 * h * k2y; sz = z + 0.5 * h * k2z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + 0.5 * h, k3x, k3y, k3z);
+    sx = x + h * k3x; sy = y + h * k3y; sz = z + h * k3z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + h, k4x, k4y, k4z);
+    const double c = h / 6.0;
+    ox = x + c * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    oy = y + c * (k1y + 2.0 * k2y + 2.0 * k3y + k4y);
+    oz = z + c * (k1z + 2.0 * k2z + 2.0 * k3z + k4z);
+    normalize3(ox, oy, oz);
+}
+
+// Mixed: stages in FP32; the displacement d = (h/6)(k1 + 2k2 + 2k3 + k4) is added to the FP64
+// node and projected in FP64, so the FP32 rounding scales with |d|, not with |x|.
+__device__ __forceinline__ void rk4_point_mixed(const Vel<float> &u, double xd, double yd, double zd,
+                                                float t1, float h, double &ox, double &oy,
+                                                double &oz) {
+    const float x = (float)xd, y = (float)yd, z = (float)zd;
+    float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
+    u(x, y, z, t1, k1x, k1y, k1z);
+    float sx = x + 0.5f * h * k1x, sy = y + 0.5f * h * k1y, sz = z + 0.5f * h * k1z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + 0.5f * h, k2x, k2y, k2z);
+    sx = x + 0.5f * h * k2x; sy = y + 0.5f * h * k2y; sz = z + 0.5f * h * k2z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + 0.5f * h, k3x, k3y, k3z);
+    sx = x + h * k3x; sy = y + h * k3y; sz = z + h * k3z;
+    normalize3(sx, sy, sz);
+    u(sx, sy, sz, t1 + h, k4x, k4y, k4z);
+    const float c = h / 6.0f;
+    ox = xd + (double)(c * (k1x + 2.0f * k2x + 2.0f * k3x + k4x));
+    oy = yd + (double)(c * (k1y + 2.0f * k2y + 2.0f * k3y + k4y));
+    oz = zd + (double)(c * (k1z + 2.0f * k2z + 2.0f * k3z + k4z));
+    normalize3(ox, oy, oz);
+}
+
+// Kernel-ready velocity parameters (deformation: p1 = pi / T_f).
+inline Vel<double> make_vel64(int kind, const double *prm) {
+    const double pi = 3.14159265358979323846;
+    Vel<double> u{kind, prm[0], prm[1], 0.0, 0.0};
+    if (kind == RBFSL_VEL_RIGID) { u.p2 = prm[2]; u.p3 = prm[3]; }
+    else u.p1 = pi / prm[1];
+    return u;
+}
+inline Vel<float> make_vel32(int kind, const double *prm) {
+    const double pi = 3.14159265358979323846;
+    Vel<float> u{kind, (float)prm[0], (float)prm[1], 0.f, 0.f};
+    if (kind == RBFSL_VEL_RIGID) { u.p2 = (float)prm[2]; u.p3 = (float)prm[3]; }
+    else u.p1 = (float)(pi / prm[1]);
+    return u;
+}
+
+__device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+// k nearest nodes of (qx, qy, qz) by one warp. bd/bi: the warp's candidate buffers (cap
+// entries, cap a power of two >= k), cnt: one shared int. On success bi[0..k) holds the node
+// indices ascending by (d2, index) and the function returns true; false if no radius in 40
+// rescalings brackets between k and cap candidates.
+__device__ __forceinline__ bool knn_warp(const KnnGrid &g, double qx, double qy, double qz, int k,
+                                         int cap, double *bd, int *bi, int *cnt, int lane) {
+    double r2 = g.r2_per_k * k;
+    const double target = 1.3 * k;
+    int total = 0;
+    bool ok = false;
+    for (int iter = 0; iter < 40; ++iter) {
+        if (lane == 0) *cnt = 0;
+        __syncwarp();
+        const double rb = sqrt(r2) * (1.0 + 1e-9) + 1e-15;
+        grid_ball_foreach(g, qx, qy, qz, rb, lane, [&](int p) {
+            const double d2 = sqdist_rn(qx, qy, qz, g.sx[p], g.sy[p], g.sz[p]);
+            if (d2 <= r2) {
+                const int slot = atomicAdd(cnt, 1);
+                if (slot < cap) {
+                    bd[slot] = d2;
+                    bi[slot] = g.sid[p];
+                }
+            }
+        });
+        __syncwarp();
+        total = *cnt;
+        __syncwarp();
+        if (total >= k && total <= cap) {
+            ok = true;
+            break;
+        }
+        // Rescale the radius towards ~1.3 k candidates (count grows like r^2).
+        double f = total > 0 ? target / (double)total : 4.0;
+        f = f < 0.25 ? 0.25 : (f > 4.0 ? 4.0 : f);
+        if (total < k && f < 1.05) f = 1.05;
+        if (total > cap && f > 0.95) f = 0.95;
+        r2 *= f;
+    }
+    if (!ok) return false;
+    // Bitonic sort of the candidates by (d2, index), padded to a power of two.
+    int P = 1;
+    while (P < total) P <<= 1;
+    for (int i = total + lane; i < P; i += kWarp) {
+        bd[i] = INFINITY;
+        bi[i] = 0x7fffffff;
+    }
+    __syncwarp();
+    for (int len = 2; len <= P; len <<= 1) {
+        for (int stride = len >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < P; i += kWarp) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & len) == 0;
+                    const double di = bd[i], dj = bd[j];
+                    const int ii = bi[i], ij = bi[j];
+                    if (key_less(dj, ij, di, ii) == up) {
+                        bd[i] = dj; bi[i] = ij;
+                        bd[j] = di; bi[j] = ii;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    return true;
+}
+
+__host__ __device__ inline int knn_cap(int k) {
+    int cap = 64;
+    while (cap < 3 * k) cap <<= 1;
+    return cap;
+}
+// Trailing update of one elimination step for the rows r0, r0 + NW, r0 + 2 NW, ... < m:
+// A[r][j] -= A[r][k] * A[k][j] for the NCH column chunks j = k+1+lane+32c <= m. NCH is a
+// compile-time count so that no FP64 instruction is issued for a chunk with no live column
+// (a predicated-off DFMA still takes an FP64 issue slot). Rows go two at a time, and the next
+// pair's operands are loaded before the current pair is stored, so shared-memory latency
+// overlaps the DFMAs.
+template <int NW, int NCH>
+__device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, int m, int k,
+                                                int r, int lane) {
+    double pk[NCH];
+    int jc[NCH];
+    bool on[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        jc[c] = k + 1 + lane + c * kWarp;
+        on[c] = jc[c] <= m;
+        pk[c] = on[c] ? A[k * ld + jc[c]] : 0.0;
+    }
+    if (r + NW < m) {
+        double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
+        double v0[NCH], v1[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            v0[c] = on[c] ? A[r * ld + jc[c]] : 0.0;
+            v1[c] = on[c] ? A[(r + NW) * ld + jc[c]] : 0.0;
+        }
+        for (;;) {
+            const int rn = r + 2 * NW;
+            const bool more = rn + NW < m;
+            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
+            if (more) {
+                nl0 = A[rn * ld + k];
+                nl1 = A[(rn + NW) * ld + k];
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                nv0[c] = (more && on[c]) ? A[rn * ld + jc[c]] : 0.0;
+                nv1[c] = (more && on[c]) ? A[(rn + NW) * ld + jc[c]] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                if (c < NCH - 1 || on[c]) {
+                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
+                    A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
+                }
+            }
+            r = rn;
+            if (!more) break;
+            l0 = nl0;
+            l1 = nl1;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                v0[c] = nv0[c];
+                v1[c] = nv1[c];
+            }
+        }
+    }
+    if (r < m) {
+        const double l0 = A[r * ld + k];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
+    }
+}
+
+
+// Shared-memory layout of one point: A (m x ld, the augmented [A~ | b] system), the stencil
+// coordinates (3 x n), the inverse pivots (m), one flag word.
+__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + m + 1; }
+
+// Weights of one point by a group of NW warps (thread t of the group, NW * 32 threads):
+// assemble [[A, P], [P^T, 0] | phi(|p - x_j|); Y(p)] (Eqs. rbf_poly, rbf_poly_linsys) in the
+// group's shared region A and eliminate with partial pivoting (largest magnitude, smaller row
+// on a tie). Returns RBFSL_OK with the solution w~ in column m of A (rows 0..m-1, valid for
+// warp 0 of the group), RBFSL_EKNN for a stencil index < 0, RBFSL_ESINGULAR for a zero or
+// non-finite pivot. Every thread of the group must call it; with NW > 1 the group is the block.
+template <int NW>
+__device__ __forceinline__ int weights_point(double *__restrict__ A, const double *__restrict__ X,
+                                             const int32_t *__restrict__ stencil, int n, int m,
+                                             int ld, int ell, int half, double px, double py,
+                                             double pz, int t) {
+    constexpr int GT = NW * kWarp;
+    const int warp = t >> 5, lane = t & 31;
+    const int M = m - n;
+    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n, *invp = cz + n;
+    int *flag = reinterpret_cast<int *>(invp + m);
+    auto gsync = [] {
+        if (NW == 1) __syncwarp(); else __syncthreads();
+    };
+    if (t == 0) *flag = 0;
+    gsync();
+    for (int j = t; j < n; j += GT) {
+        const int64_t s = stencil[j];
+        if (s < 0) { *flag = 1; continue; }  // a failed neighbour search leaves -1
+        cx[j] = X[3 * s];
+        cy[j] = X[3 * s + 1];
+        cz[j] = X[3 * s + 2];
+    }
+    gsync();
+    if (*flag) return RBFSL_EKNN;
+
+    // ---- assembly. RBF block: the n(n-1)/2 pairs j < k are folded into rows of n-1 pairs
+    // (row f and row n-1-f together) so that every thread has work.
+    const int P2 = n * (n - 1) / 2;
+    for (int p = t; p < P2; p += GT) {
+        const int f = p / (n - 1), e = p - f * (n - 1);
+        int r, c;
+        if (e < n - 1 - f) { r = f; c = f + 1 + e; } else { r = n - 1 - f; c = e + 1; }
+        const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
+        const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
+        A[r * ld + c] = v;
+        A[c * ld + r] = v;
+    }
+    for (int j = t; j < n; j += GT) {
+        A[j * ld + j] = 0.0;
+        sh_eval(ell, cx[j], cy[j], cz[j], [&](int c, double v) {
+            A[j * ld + n + c] = v;
+            A[(n + c) * ld + j] = v;
+        });
+        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
+        A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
+    }
+    for (int e = t; e < M * M; e += GT) A[(n + e / M) * ld + n + e % M] = 0.0;
+    if (t == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
+    gsync();
+
+    // ---- Gaussian elimination with partial pivoting on [A~ | b]
+    for (int k = 0; k < m; ++k) {
+        if (warp == 0) {
+            // pivot: largest |a_rk| (integer compare of the magnitude bits), smaller row on a tie
+            long long best = -1;
+            int bidx = m;
+            for (int r = k + lane; r < m; r += kWarp) {
+                const long long v = __double_as_longlong(A[r * ld + k]) & 0x7fffffffffffffffLL;
+                if (v > best) { best = v; bidx = r; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
+                if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+            }
+            if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
+                if (lane == 0) *flag = 2;
+            } else {
+                if (bidx != k) {
+                    for (int c = k + lane; c <= m; c += kWarp) {
+                        const double tmp = A[k * ld + c];
+                        A[k * ld + c] = A[bidx * ld + c];
+                        A[bidx * ld + c] = tmp;
+                    }
+                    __syncwarp();
+                }
+                const double inv = 1.0 / A[k * ld + k];
+                if (lane == 0) invp[k] = inv;
+                for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
+            }
+        }
+        gsync();
+        if (*flag) return RBFSL_ESINGULAR;
+        // trailing update: rows k+1.. cyclic over the NW warps, lanes over the m - k columns
+        // k+1..m in chunks of 32 (pivot row in registers)
+        switch ((m - k + kWarp - 1) / kWarp) {
+            case 1: trailing_update<NW, 1>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 2: trailing_update<NW, 2>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 3: trailing_update<NW, 3>(A, ld, m, k, k + 1 + warp, lane); break;
+            case 4: trailing_update<NW, 4>(A, ld, m, k, k + 1 + warp, lane); break;
+            default: trailing_update<NW, 5>(A, ld, m, k, k + 1 + warp, lane); break;
+        }
+        gsync();
+    }
+    if (warp != 0) return RBFSL_OK;
+    // ---- back substitution on the rhs column (warp 0), with the stored inverse pivots
+    for (int r = m - 1; r >= 0; --r) {
+        const double xr = A[r * ld + m] * invp[r];
+        __syncwarp();
+        if (lane == 0) A[r * ld + m] = xr;
+        for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
+        __syncwarp();
+    }
+    return RBFSL_OK;
+}
+
+// Centre-stencil weights of one point by one warp (Sec. 3.3): the point uses the stencil
+// S = Ik[k] of its nearest node k, whose m x m saddle-point matrix was factorised once
+// (row-major LU F, row order pr). b = [phi(|p - x_Sj|); Y(p)], then L U w~ = P b with row-wise
+// dot products (lanes over a contiguous factor row, warp-shuffle sums). b and y: 2 m shared
+// doubles of the warp. On return y[0..n) holds the weights (all lanes).
+__device__ __forceinline__ void center_point(const double *__restrict__ X, const int32_t *__restrict__ S,
+                                             const double *__restrict__ F, const int32_t *__restrict__ pr,
+                                             int n, int m, int ell, int half, double px, double py,
+                                             double pz, double *b, double *y, int lane) {
+    for (int j = lane; j < n; j += 32) {
+        const int64_t s = S[j];
+        const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
+        b[j] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
+    }
+    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { b[n + c] = v; });
+    __syncwarp();
+    for (int r = lane; r < m; r += 32) y[r] = b[pr[r]];
+    __syncwarp();
+    for (int r = 1; r < m; ++r) {  // forward: y_r -= sum_{c<r} L_rc y_c (unit lower)
+        double s = 0.0;
+        for (int c = lane; c < r; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[r] -= s;
+        __syncwarp();
+    }
+    for (int r = m - 1; r >= 0; --r) {  // backward: y_r = (y_r - sum_{c>r} U_rc y_c) / U_rr
+        double s = 0.0;
+        for (int c = r + 1 + lane; c < m; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[r] = (y[r] - s) / F[(size_t)r * m + r];
+        __syncwarp();
+    }
+}
+
+// One output row of the gather-dot for tracer lanes t = lane, lane + 32, ... < T, with the
+// weights w[0..n) and stencil S[0..n) of the row (shared or global memory). FP64:
+// sum_j w_j q[S_j][t]; FP32: difference form q_c + sum_j w_j (q_j - q_c), c = S[0]. The
+// summation runs over j in stencil order (the same order as gather_dot_kernel).
+template <typename R, typename W>
+__device__ __forceinline__ void gather_row(const W *__restrict__ w, const int32_t *__restrict__ S, int n,
+                                           const R *__restrict__ q, int T, R *__restrict__ out, int lane) {
+    for (int t = lane; t < T; t += 32) {
+        R acc = R(0);
+        if (sizeof(R) == 8) {
+            for (int j = 0; j < n; ++j) acc = fma((R)w[j], q[(int64_t)S[j] * T + t], acc);
+            out[t] = acc;
+        } else {
+            const R qc = q[(int64_t)S[0] * T + t];
+            for (int j = 0; j < n; ++j) acc = fma((R)w[j], q[(int64_t)S[j] * T + t] - qc, acc);
+            out[t] = qc + acc;
+        }
+    }
+}
+
+}  // namespace rbfsl

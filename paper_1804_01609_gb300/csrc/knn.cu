@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "device_ops.cuh"
 
 namespace rbfsl {
 
@@ -126,10 +127,6 @@ void knn_index_free(rbfsl_knn_index *ix) {
     ix->sid = ix->cell_start = nullptr;
 }
 
-__device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
-    return da < db || (da == db && ia < ib);
-}
-
 // One warp per query. Shared memory per warp: cap doubles + cap ints + 1 counter.
 __global__ void __launch_bounds__(128) knn_query_kernel(KnnGrid g, const double *__restrict__ Q,
                                                         int64_t Nq, int k, int cap,
@@ -145,78 +142,15 @@ __global__ void __launch_bounds__(128) knn_query_kernel(KnnGrid g, const double 
                (size_t)wpb * cap + warp;
     const int64_t q = (int64_t)blockIdx.x * wpb + warp;
     if (q >= Nq) return;
-    const double qx = Q[3 * q], qy = Q[3 * q + 1], qz = Q[3 * q + 2];
-    double r2 = g.r2_per_k * k;
-    const double target = 1.3 * k;
-    int total = 0;
-    bool ok = false;
-    for (int iter = 0; iter < 40; ++iter) {
-        if (lane == 0) *cnt = 0;
-        __syncwarp();
-        const double rb = sqrt(r2) * (1.0 + 1e-9) + 1e-15;
-        grid_ball_foreach(g, qx, qy, qz, rb, lane, [&](int p) {
-            const double d2 = sqdist_rn(qx, qy, qz, g.sx[p], g.sy[p], g.sz[p]);
-            if (d2 <= r2) {
-                const int slot = atomicAdd(cnt, 1);
-                if (slot < cap) {
-                    bd[slot] = d2;
-                    bi[slot] = g.sid[p];
-                }
-            }
-        });
-        __syncwarp();
-        total = *cnt;
-        __syncwarp();
-        if (total >= k && total <= cap) {
-            ok = true;
-            break;
-        }
-        // Rescale the radius towards ~1.3 k candidates (count grows like r^2).
-        double f = total > 0 ? target / (double)total : 4.0;
-        f = f < 0.25 ? 0.25 : (f > 4.0 ? 4.0 : f);
-        if (total < k && f < 1.05) f = 1.05;
-        if (total > cap && f > 0.95) f = 0.95;
-        r2 *= f;
-    }
-    if (!ok) {
-        for (int r = lane; r < k; r += kWarp) idx[q * k + r] = -1;
-        if (status && lane == 0) status[q] = RBFSL_EKNN;
-        return;
-    }
-    // Bitonic sort of the candidates by (d2, index), padded to a power of two.
-    int P = 1;
-    while (P < total) P <<= 1;
-    for (int i = total + lane; i < P; i += kWarp) {
-        bd[i] = INFINITY;
-        bi[i] = 0x7fffffff;
-    }
-    __syncwarp();
-    for (int len = 2; len <= P; len <<= 1) {
-        for (int stride = len >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < P; i += kWarp) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & len) == 0;
-                    const double di = bd[i], dj = bd[j];
-                    const int ii = bi[i], ij = bi[j];
-                    if (key_less(dj, ij, di, ii) == up) {
-                        bd[i] = dj; bi[i] = ij;
-                        bd[j] = di; bi[j] = ii;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    for (int r = lane; r < k; r += kWarp) idx[q * k + r] = bi[r];
-    if (status && lane == 0) status[q] = RBFSL_OK;
+    const bool ok = knn_warp(g, Q[3 * q], Q[3 * q + 1], Q[3 * q + 2], k, cap, bd, bi, cnt, lane);
+    for (int r = lane; r < k; r += kWarp) idx[q * k + r] = ok ? bi[r] : -1;
+    if (status && lane == 0) status[q] = ok ? RBFSL_OK : RBFSL_EKNN;
 }
 
 int launch_knn(const rbfsl_knn_index *ix, const double *q, int64_t Nq, int k, int32_t *idx,
                int32_t *status, cudaStream_t s) {
     if (Nq == 0) return RBFSL_OK;
-    int cap = 64;
-    while (cap < 3 * k) cap <<= 1;
+    const int cap = knn_cap(k);
     const int wpb = 4;
     const size_t smem = (size_t)wpb * cap * (sizeof(double) + sizeof(int)) + wpb * sizeof(int);
     const KnnGrid g = grid_view(ix);

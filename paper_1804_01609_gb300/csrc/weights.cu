@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "device_ops.cuh"
 
 namespace rbfsl {
 
@@ -61,197 +62,23 @@ struct WeightsArgs {
     int32_t *status;
 };
 
-// Shared-memory layout of one point: A (m x ld, the augmented [A~ | b] system), the stencil
-// coordinates (3 x n), the inverse pivots (m), one flag word.
-__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + m + 1; }
-
-// Trailing update of one elimination step for the rows r0, r0 + NW, r0 + 2 NW, ... < m:
-// A[r][j] -= A[r][k] * A[k][j] for the NCH column chunks j = k+1+lane+32c <= m. NCH is a
-// compile-time count so that no FP64 instruction is issued for a chunk with no live column
-// (a predicated-off DFMA still takes an FP64 issue slot). Rows go two at a time, and the next
-// pair's operands are loaded before the current pair is stored, so shared-memory latency
-// overlaps the DFMAs.
-template <int NW, int NCH>
-__device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, int m, int k,
-                                                int r, int lane) {
-    double pk[NCH];
-    int jc[NCH];
-    bool on[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        jc[c] = k + 1 + lane + c * kWarp;
-        on[c] = jc[c] <= m;
-        pk[c] = on[c] ? A[k * ld + jc[c]] : 0.0;
-    }
-    if (r + NW < m) {
-        double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
-        double v0[NCH], v1[NCH];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            v0[c] = on[c] ? A[r * ld + jc[c]] : 0.0;
-            v1[c] = on[c] ? A[(r + NW) * ld + jc[c]] : 0.0;
-        }
-        for (;;) {
-            const int rn = r + 2 * NW;
-            const bool more = rn + NW < m;
-            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
-            if (more) {
-                nl0 = A[rn * ld + k];
-                nl1 = A[(rn + NW) * ld + k];
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                nv0[c] = (more && on[c]) ? A[rn * ld + jc[c]] : 0.0;
-                nv1[c] = (more && on[c]) ? A[(rn + NW) * ld + jc[c]] : 0.0;
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (c < NCH - 1 || on[c]) {
-                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
-                    A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
-                }
-            }
-            r = rn;
-            if (!more) break;
-            l0 = nl0;
-            l1 = nl1;
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                v0[c] = nv0[c];
-                v1[c] = nv1[c];
-            }
-        }
-    }
-    if (r < m) {
-        const double l0 = A[r * ld + k];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c)
-            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
-    }
-}
-
-// NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
-// the group barrier is __syncwarp; with NW = 4 a block is one point and uses __syncthreads.
+// NW warps per point (1, 4 or 8). With NW = 1 a block holds blockDim/32 independent points and
+// the group barrier is __syncwarp; with NW > 1 a block is one point and uses __syncthreads.
 template <int NW, typename WT>
 __global__ void __launch_bounds__(NW == 8 ? 256 : 128) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
     extern __shared__ double smem[];
     constexpr int GT = NW * kWarp;
     const int g = threadIdx.x / GT, t = threadIdx.x % GT;
-    const int warp = t >> 5, lane = t & 31;
     const int spb = blockDim.x / GT;
     const int64_t i = (int64_t)blockIdx.x * spb + g;
     if (i >= a.Nq) return;  // NW == 1 only (with NW > 1 the grid has exactly Nq blocks)
-    const int n = a.n, m = a.m, ld = a.ld, M = m - n;
     double *A = smem + (size_t)g * a.stencil_doubles;
-    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n, *invp = cz + n;
-    int *flag = reinterpret_cast<int *>(invp + m);
-    auto gsync = [] {
-        if (NW == 1) __syncwarp(); else __syncthreads();
-    };
-
-    if (t == 0) *flag = 0;
-    gsync();
-    for (int j = t; j < n; j += GT) {
-        const int64_t s = a.idx[i * n + j];
-        if (s < 0) { *flag = 1; continue; }  // a failed neighbour search leaves -1
-        cx[j] = a.X[3 * s];
-        cy[j] = a.X[3 * s + 1];
-        cz[j] = a.X[3 * s + 2];
-    }
-    gsync();
-    if (*flag) {
-        for (int j = t; j < n; j += GT) W[i * n + j] = (WT)NAN;
-        if (a.status && t == 0) a.status[i] = RBFSL_EKNN;
-        return;
-    }
-    const double px = a.P[3 * i], py = a.P[3 * i + 1], pz = a.P[3 * i + 2];
-
-    // ---- assembly. RBF block: the n(n-1)/2 pairs j < k are folded into rows of n-1 pairs
-    // (row f and row n-1-f together) so that every thread has work.
-    const int P2 = n * (n - 1) / 2;
-    for (int p = t; p < P2; p += GT) {
-        const int f = p / (n - 1), e = p - f * (n - 1);
-        int r, c;
-        if (e < n - 1 - f) { r = f; c = f + 1 + e; } else { r = n - 1 - f; c = e + 1; }
-        const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
-        const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
-        A[r * ld + c] = v;
-        A[c * ld + r] = v;
-    }
-    for (int j = t; j < n; j += GT) {
-        A[j * ld + j] = 0.0;
-        sh_eval(a.ell, cx[j], cy[j], cz[j], [&](int c, double v) {
-            A[j * ld + n + c] = v;
-            A[(n + c) * ld + j] = v;
-        });
-        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
-        A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, a.half);
-    }
-    for (int e = t; e < M * M; e += GT) A[(n + e / M) * ld + n + e % M] = 0.0;
-    if (t == 0) sh_eval(a.ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
-    gsync();
-
-    // ---- Gaussian elimination with partial pivoting on [A~ | b]
-    for (int k = 0; k < m; ++k) {
-        if (warp == 0) {
-            // pivot: largest |a_rk| (integer compare of the magnitude bits), smaller row on a tie
-            long long best = -1;
-            int bidx = m;
-            for (int r = k + lane; r < m; r += kWarp) {
-                const long long v = __double_as_longlong(A[r * ld + k]) & 0x7fffffffffffffffLL;
-                if (v > best) { best = v; bidx = r; }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
-                if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-            }
-            if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
-                if (lane == 0) *flag = 2;
-            } else {
-                if (bidx != k) {
-                    for (int c = k + lane; c <= m; c += kWarp) {
-                        const double tmp = A[k * ld + c];
-                        A[k * ld + c] = A[bidx * ld + c];
-                        A[bidx * ld + c] = tmp;
-                    }
-                    __syncwarp();
-                }
-                const double inv = 1.0 / A[k * ld + k];
-                if (lane == 0) invp[k] = inv;
-                for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
-            }
-        }
-        gsync();
-        if (*flag) break;
-        // trailing update: rows k+1.. cyclic over the NW warps, lanes over the m - k columns
-        // k+1..m in chunks of 32 (pivot row in registers)
-        switch ((m - k + kWarp - 1) / kWarp) {
-            case 1: trailing_update<NW, 1>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 2: trailing_update<NW, 2>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 3: trailing_update<NW, 3>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 4: trailing_update<NW, 4>(A, ld, m, k, k + 1 + warp, lane); break;
-            default: trailing_update<NW, 5>(A, ld, m, k, k + 1 + warp, lane); break;
-        }
-        gsync();
-    }
-    if (warp != 0) return;
-    if (*flag) {
-        for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)NAN;
-        if (a.status && lane == 0) a.status[i] = RBFSL_ESINGULAR;
-        return;
-    }
-    // ---- back substitution on the rhs column (warp 0), with the stored inverse pivots
-    for (int r = m - 1; r >= 0; --r) {
-        const double xr = A[r * ld + m] * invp[r];
-        __syncwarp();
-        if (lane == 0) A[r * ld + m] = xr;
-        for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
-        __syncwarp();
-    }
-    for (int j = lane; j < n; j += kWarp) W[i * n + j] = (WT)A[j * ld + m];
-    if (a.status && lane == 0) a.status[i] = RBFSL_OK;
+    const int rc = weights_point<NW>(A, a.X, a.idx + i * a.n, a.n, a.m, a.ld, a.ell, a.half,
+                                     a.P[3 * i], a.P[3 * i + 1], a.P[3 * i + 2], t);
+    if (t >= kWarp) return;
+    const int n = a.n, lane = t;
+    for (int j = lane; j < n; j += kWarp) W[i * n + j] = rc == RBFSL_OK ? (WT)A[j * a.ld + a.m] : (WT)NAN;
+    if (a.status && lane == 0) a.status[i] = rc;
 }
 
 template <int NW, typename WT>
@@ -295,12 +122,8 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
                                 : launch_weights_nw<1, float>(a, spb, w, s);
 }
 
-// Centre-stencil weights (Sec. 3.3): the departure point p_i uses the stencil of its nearest
-// node K_i, whose saddle-point matrix was factorised once (row-major LU of the m x m system,
-// row order perm). Per point: b = [phi(|p - x_Sj|); Y(p)], then L U w~ = P b with row-wise
-// dot products (lanes over a contiguous factor row, warp-shuffle sums); w = w~[0:n]. One warp
-// per point; the factor rows are streamed once, so the kernel is bound by HBM bandwidth
-// (8 m^2 bytes per point) and the FP64 rate (2 m^2 flops per point).
+// Centre-stencil weights, one warp per point (see center_point): bound by HBM bandwidth
+// (8 m^2 bytes of factor per point) and the FP64 rate (2 m^2 flops per point).
 template <typename WT>
 __global__ void __launch_bounds__(128) center_weights_kernel(
     const double *__restrict__ X, const int32_t *__restrict__ Kc, const int32_t *__restrict__ Ik,
@@ -319,37 +142,9 @@ __global__ void __launch_bounds__(128) center_weights_kernel(
         if (status && lane == 0) status[i] = RBFSL_EKNN;
         return;
     }
-    const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-    for (int j = lane; j < n; j += 32) {
-        const int64_t s = Ik[k * n + j];
-        I[i * n + j] = (int32_t)s;
-        const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
-        b[j] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
-    }
-    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { b[n + c] = v; });
-    __syncwarp();
-    const double *F = LU + (size_t)k * m * m;
-    const int32_t *pr = perm + (size_t)k * m;
-    for (int r = lane; r < m; r += 32) y[r] = b[pr[r]];
-    __syncwarp();
-    // forward: y_r -= sum_{c<r} L_rc y_c (unit lower)
-    for (int r = 1; r < m; ++r) {
-        double s = 0.0;
-        for (int c = lane; c < r; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[r] -= s;
-        __syncwarp();
-    }
-    // backward: y_r = (y_r - sum_{c>r} U_rc y_c) / U_rr
-    for (int r = m - 1; r >= 0; --r) {
-        double s = 0.0;
-        for (int c = r + 1 + lane; c < m; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[r] = (y[r] - s) / F[(size_t)r * m + r];
-        __syncwarp();
-    }
+    for (int j = lane; j < n; j += 32) I[i * n + j] = Ik[k * n + j];
+    center_point(X, Ik + k * n, LU + (size_t)k * m * m, perm + (size_t)k * m, n, m, ell, half,
+                 P[3 * i], P[3 * i + 1], P[3 * i + 2], b, y, lane);
     for (int j = lane; j < n; j += 32) W[i * n + j] = (WT)y[j];
     if (status && lane == 0) status[i] = RBFSL_OK;
 }

@@ -243,6 +243,7 @@ def batched_problems(P: int = 64, seed: int = SEED_BASE + 4):
                                                       float(rng.uniform(0.5, 2.0)))
         else:
             vk, vp = VEL_DEFORM_Y2, deformation_params(float(rng.uniform(1.5, 2.5)), 1.0)
-        out.append(dict(N=N, n=n, ell=ell, power=5 if ell > 2 else 3, T=T, vel_kind=vk,
+        # PHS exponent by the paper's rule k = L (Sec. 2.4): r^(2 ell + 1)
+        out.append(dict(N=N, n=n, ell=ell, power=2 * ell + 1, T=T, vel_kind=vk,
                         vel_params=vp, seed=int(seed * 1000 + p)))
     return out

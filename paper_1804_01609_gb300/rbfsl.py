@@ -67,6 +67,15 @@ SIGNATURES = {
     "rbfsl_pu_destroy": (_I, [_P]),
     "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
     "rbfsl_set_pu": (_I, [_P, _P, _I64, _D, _I, _I]),
+    "rbfsl_batch_create": (_I, [_P, _I, _P]),
+    "rbfsl_batch_destroy": (_I, [_P]),
+    "rbfsl_batch_add": (_I, [_P, _P, _P]),
+    "rbfsl_batch_remove": (_I, [_P, _I]),
+    "rbfsl_batch_step": (_I, [_P, _I]),
+    "rbfsl_batch_get_q": (_I, [_P, _I, _P]),
+    "rbfsl_batch_problem_stats": (_I, [_P, _I, _P]),
+    "rbfsl_batch_set_graph": (_I, [_P, _I]),
+    "rbfsl_batch_autotune": (_I, [_P, _P, _I]),
     "rbfsl_create": (_I, [_P, _I, _P]),
     "rbfsl_destroy": (_I, [_P]),
     "rbfsl_set_nodes": (_I, [_P, _P, _I64, _I]),
@@ -249,6 +258,77 @@ def rbfsl_pu_apply(pu, q, p, weight_kind, out, status=None, stream=None):
     T = q.shape[1] if q.dim() == 2 else 1
     _check(load().rbfsl_pu_apply(pu.handle, _ptr(q), T, _ptr(p), p.shape[0], weight_kind,
                                  _dtype_code(out), _ptr(out), _ptr(status), _stream(stream)))
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("nodes", ctypes.c_void_p), ("n", ctypes.c_int),
+                ("ell", ctypes.c_int), ("phs_power", ctypes.c_double), ("mode", ctypes.c_int),
+                ("precision", ctypes.c_int), ("vel_kind", ctypes.c_int),
+                ("vel_params", ctypes.c_double * 4), ("t0", ctypes.c_double),
+                ("dt", ctypes.c_double), ("T", ctypes.c_int), ("q0", ctypes.c_void_p)]
+
+
+class Batch:
+    """Many local problems stepped together (rbfsl_batch_*)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        _check(load().rbfsl_batch_create(ctypes.byref(self._h), device,
+                                         _stream(stream) if stream is not None else 0))
+
+    def add(self, X, q0, n, ell, power, vel_kind, vel_params, dt, mode=DIRECT, precision=FP64, t0=0.0):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        q = np.ascontiguousarray(np.asarray(q0, dtype=np.float64).reshape(X.shape[0], -1))
+        vp = (ctypes.c_double * 4)(*(list(np.asarray(vel_params, dtype=float)) + [0.0] * 4)[:4])
+        p = Problem(X.shape[0], X.ctypes.data, n, ell, float(power), mode, precision, vel_kind, vp,
+                    float(t0), float(dt), q.shape[1], q.ctypes.data)
+        pid = ctypes.c_int()
+        _check(load().rbfsl_batch_add(self._h, ctypes.byref(p), ctypes.byref(pid)))
+        self._keep[pid.value] = (X.shape[0], q.shape[1])
+        return pid.value
+
+    def remove(self, pid):
+        _check(load().rbfsl_batch_remove(self._h, pid))
+        self._keep.pop(pid, None)
+
+    def step(self, nsteps=1):
+        _check(load().rbfsl_batch_step(self._h, nsteps))
+
+    def get_q(self, pid):
+        N, T = self._keep[pid]
+        out = np.empty((N, T))
+        _check(load().rbfsl_batch_get_q(self._h, pid, out.ctypes.data))
+        return out
+
+    def stats(self, pid) -> Stats:
+        s = Stats()
+        _check(load().rbfsl_batch_problem_stats(self._h, pid, ctypes.byref(s)))
+        return s
+
+    def set_graph(self, use):
+        _check(load().rbfsl_batch_set_graph(self._h, int(bool(use))))
+
+    def autotune(self):
+        buf = (ctypes.c_int * 96)()
+        _check(load().rbfsl_batch_autotune(self._h, buf, 96))
+        out = []
+        for i in range(0, 96, 3):
+            if buf[i] == 0:
+                break
+            out.append((buf[i], buf[i + 1], buf[i + 2]))
+        return out
+
+    def close(self):
+        if self._h:
+            load().rbfsl_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # --------------------------------------------------------------------------- context
