@@ -49,7 +49,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC",
+    # -fmad=false: no implicit contraction of a*b+c into FMA. The hot loops use explicit fma();
+    # everything else is rounded operation by operation, so the same device code gives the same
+    # bits in every kernel it is inlined into (single problem, batch, server).
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-fmad=false", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC] + list(extra_flags)
 
     def compile_one(src):

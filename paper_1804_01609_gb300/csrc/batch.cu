@@ -607,7 +607,12 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
     for (long long key : classes) {
         float best_ms = 1e30f;
         int best = 4;
+        int max_smem = 0;
+        RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+        const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
+        const int per_bytes = batch_point_doubles(kn, km, (km + 1) | 1, knn_cap(kn)) * 8;
         for (int ppt : {4, 1}) {
+            if (ppt == 4 && 4 * per_bytes > max_smem) continue;  // four points do not fit on chip
             // only this class active, with the candidate tile shape
             std::vector<int> saved;
             for (auto &h : b->probs) {
