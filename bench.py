@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--accuracy-steps", type=int, default=600,
                     help="steps of the full-trajectory accuracy runs (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
     ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
@@ -220,6 +222,96 @@ def cpu_baseline(w, budget_s=10.0):
     return {"value": S / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"{S} of {w.N} node-updates of one SL step (brute-force k-NN, GEPP, "
                       f"gather of {w.T} tracers; FP64 C + OpenMP); {el:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- batched
+def bench_batched(rbfsl, torch, stream, precision, steps=2):
+    """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
+    {(31,2), (55,3), (84,4)} with r^(2 ell + 1), 1-16 tracers, own rotation or deformation),
+    direct stencils, one persistent fused kernel per step under a CUDA graph."""
+    from paper_1804_01609_gb300 import inputs
+    specs = inputs.batched_problems(64)
+    b = rbfsl.Batch(0, stream=stream)
+    nodes = 0
+    for sp in specs:
+        X = inputs.nodes(sp["N"], sp["seed"])
+        rng = np.random.default_rng(sp["seed"])
+        fns = [inputs.plane_wave_field(rng, 8.0) for _ in range(sp["T"])]
+        q0 = np.stack([f(X) for f in fns], axis=1)
+        b.add(X, q0, sp["n"], sp["ell"], sp["power"], sp["vel_kind"], sp["vel_params"], 1.0 / 100,
+              mode=rbfsl.DIRECT, precision=precision)
+        nodes += sp["N"]
+    choices = b.autotune()
+    b.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    b.close()
+    return {"problems": len(specs), "nodes": nodes, "value": nodes / (ms / 1e3), "ms_per_step": ms,
+            "tile_shapes": [list(c) for c in choices]}
+
+
+# ----------------------------------------------------------------------------- served
+def bench_served(rbfsl, precision, R=32, rate=200.0, seed=1804 * 100 + 5):
+    """Poisson arrivals (mean `rate`/s) of R transport solves, half local (centre stencils,
+    (n, ell) from {(31,2),(55,3),(84,4)}) and half RBF-PU (~100 nodes per patch, ell = 3), N from
+    {642, 2562, 10242, 40962}, 1-16 tracers, 50-200 steps; device-memory budget 150 GB."""
+    import threading
+    from paper_1804_01609_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    reqs = []
+    t = 0.0
+    for k in range(R):
+        t += rng.exponential(1.0 / rate)
+        N = int(rng.choice([642, 2562, 10242, 40962]))
+        T = int(rng.integers(1, 17))
+        steps = int(rng.integers(50, 201))
+        X = inputs.nodes(N, seed * 100 + k)
+        fns = [inputs.plane_wave_field(rng, 8.0) for _ in range(T)]
+        q0 = np.stack([f(X) for f in fns], axis=1)
+        vp = inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], float(rng.uniform(0.5, 2.0)))
+        if k % 2 == 0:
+            n, ell = [(31, 2), (55, 3), (84, 4)][int(rng.integers(0, 3))]
+            reqs.append((t, dict(X=X, q0=q0, n=n, ell=ell, power=2 * ell + 1, vel_kind=0, vel_params=vp,
+                                 dt=1.0 / steps, steps=steps, method=rbfsl.LOCAL, mode=rbfsl.CENTER,
+                                 precision=precision, centers=None)))
+        else:
+            n = 100
+            C = inputs.fibonacci_nodes(int(np.ceil(2.5 * N / n)))
+            reqs.append((t, dict(X=X, q0=q0, n=n, ell=3, power=7, vel_kind=0, vel_params=vp,
+                                 dt=1.0 / steps, steps=steps, method=rbfsl.PU, mode=rbfsl.DIRECT,
+                                 precision=precision, centers=C)))
+    srv = rbfsl.Server(0, budget_bytes=150 * 10 ** 9, max_slots=64)
+    tickets = []
+
+    def submitter():
+        t0 = time.perf_counter()
+        for ta, r in reqs:
+            d = ta - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(r["X"], r["q0"], r["n"], r["ell"], r["power"], r["vel_kind"],
+                                      r["vel_params"], r["dt"], r["steps"], method=r["method"],
+                                      mode=r["mode"], precision=r["precision"], centers=r["centers"]))
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    srv.wait_idle(1200)
+    stats = [srv.result(tk)[1] for tk in tickets]
+    info = srv.info()
+    srv.close()
+    lat = np.array([s.finish_s - s.submit_s for s in stats])
+    span = max(s.finish_s for s in stats) - min(s.submit_s for s in stats)
+    nu = sum(s.node_updates for s in stats)
+    return {"requests": R, "arrival_rate_per_s": rate, "node_updates": int(nu),
+            "value": nu / span, "wall_s": span, "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)), "failed": int(sum(s.status != 0 for s in stats)),
+            "peak_bytes": int(info.peak_bytes), "ticks": int(info.ticks)}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -410,6 +502,14 @@ def main():
             center["fp64"]["l2_vs_exact"] = rel_l2(qc64, q0)
             center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
+    batched = {}
+    if not args.no_batched:
+        batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),
+                   "fp64": bench_batched(rbfsl, torch, stream, rbfsl.FP64)}
+    served = {}
+    if not args.no_served:
+        served = {"mixed": bench_served(rbfsl, rbfsl.MIXED), "fp64": bench_served(rbfsl, rbfsl.FP64)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -431,6 +531,8 @@ def main():
                             "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
         "center_stencils": center,
+        "batched_64_problems": batched,
+        "served": served,
         "accuracy": acc,
         "clocks": clk.summary(),
         "e2e": e2e,

@@ -299,6 +299,54 @@ int rbfsl_batch_set_graph(rbfsl_batch *b, int use_graph);
  * (n, ell, points per tile: 4 = one warp per point, 1 = four warps per point). */
 int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices);
 
+/* ================================================================== serving */
+/* A serving loop for transport solves on one GPU. Requests (a full problem plus a step count)
+ * are submitted at any time from any thread and copied. A scheduler thread owned by the
+ * server repeats ticks: admit queued requests in arrival order while each fits the
+ * device-memory budget and a slot is free; advance every running request by one SL step
+ * (all local-stencil requests together in one batched persistent launch, every RBF-PU request
+ * on its own stream, so their work overlaps on the device); retire the finished ones (field
+ * copied out, device memory freed, latency recorded). State stays on the device between steps.
+ * A request's result is bit-identical alone and in any mix. */
+typedef struct rbfsl_server rbfsl_server;
+typedef struct rbfsl_request {
+    int method;               /* RBFSL_LOCAL or RBFSL_PU */
+    rbfsl_problem problem;    /* for PU: n = nodes per patch, mode ignored */
+    int steps;                /* SL steps to run */
+    const double *pu_centers; /* PU: HOST Mp x 3, copied */
+    int64_t pu_Mp;
+    double pu_radius;         /* PU: <= 0 selects 2 sqrt(n / N) */
+    int pu_weight;            /* PU: RBFSL_PU_WENDLAND or RBFSL_PU_BSPLINE */
+} rbfsl_request;
+typedef struct rbfsl_request_stats {
+    double submit_s, admit_s, finish_s; /* seconds since the server was created */
+    int64_t steps, node_updates;
+    size_t device_bytes;                /* the admission estimate charged to the budget */
+    int status;                         /* RBFSL_OK or the failure code */
+} rbfsl_request_stats;
+typedef struct rbfsl_server_info_t {
+    int64_t ticks, queued;
+    int running;
+    size_t budget_bytes, used_bytes, peak_bytes;
+    double now_s;
+} rbfsl_server_info_t;
+/* budget: device bytes the running requests may hold together (admission estimate per request:
+ * nodes, departure points, fields, index, stencil or patch factors). max_slots: concurrent
+ * requests. Starts the scheduler thread. Errors: EINVAL, ECUDA, ENOMEM. */
+int rbfsl_server_create(rbfsl_server **out, int device, size_t hbm_budget_bytes, int max_slots);
+/* Stop the scheduler and free everything (running requests are dropped). */
+int rbfsl_server_destroy(rbfsl_server *s);
+/* Queue a request; ENOMEM if it alone exceeds the budget. Thread-safe. */
+int rbfsl_server_submit(rbfsl_server *s, const rbfsl_request *r, uint64_t *ticket);
+/* state: 0 queued, 1 running, 2 done, < 0 failed (an RBFSL_E* code). */
+int rbfsl_server_poll(rbfsl_server *s, uint64_t ticket, int *state);
+/* Collect a finished request: its field (N x T FP64, HOST, may be NULL) and statistics; the
+ * ticket is released. EINVAL while it is queued or running; the failure code if it failed. */
+int rbfsl_server_result(rbfsl_server *s, uint64_t ticket, double *q_out, rbfsl_request_stats *st);
+/* Block until no request is queued or running, or timeout_s passes (ETIMEDOUT). */
+int rbfsl_server_wait_idle(rbfsl_server *s, double timeout_s);
+int rbfsl_server_info(rbfsl_server *s, rbfsl_server_info_t *out);
+
 /* Message of the last failed call on this context (thread-local when ctx is NULL). */
 const char *rbfsl_last_error(const rbfsl_ctx *ctx);
 const char *rbfsl_version(void);

@@ -76,6 +76,13 @@ SIGNATURES = {
     "rbfsl_batch_problem_stats": (_I, [_P, _I, _P]),
     "rbfsl_batch_set_graph": (_I, [_P, _I]),
     "rbfsl_batch_autotune": (_I, [_P, _P, _I]),
+    "rbfsl_server_create": (_I, [_P, _I, ctypes.c_size_t, _I]),
+    "rbfsl_server_destroy": (_I, [_P]),
+    "rbfsl_server_submit": (_I, [_P, _P, _P]),
+    "rbfsl_server_poll": (_I, [_P, ctypes.c_uint64, _P]),
+    "rbfsl_server_result": (_I, [_P, ctypes.c_uint64, _P, _P]),
+    "rbfsl_server_wait_idle": (_I, [_P, _D]),
+    "rbfsl_server_info": (_I, [_P, _P]),
     "rbfsl_create": (_I, [_P, _I, _P]),
     "rbfsl_destroy": (_I, [_P]),
     "rbfsl_set_nodes": (_I, [_P, _P, _I64, _I]),
@@ -322,6 +329,80 @@ class Batch:
     def close(self):
         if self._h:
             load().rbfsl_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("problem", Problem), ("steps", ctypes.c_int),
+                ("pu_centers", ctypes.c_void_p), ("pu_Mp", ctypes.c_int64),
+                ("pu_radius", ctypes.c_double), ("pu_weight", ctypes.c_int)]
+
+
+class RequestStats(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("node_updates", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("status", ctypes.c_int)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int),
+                ("budget_bytes", ctypes.c_size_t), ("used_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("now_s", ctypes.c_double)]
+
+
+class Server:
+    """Serving loop with continuous batching (rbfsl_server_*)."""
+
+    def __init__(self, device=0, budget_bytes=150 * 10 ** 9, max_slots=64):
+        self._h = ctypes.c_void_p()
+        self._shape = {}
+        _check(load().rbfsl_server_create(ctypes.byref(self._h), device, int(budget_bytes), max_slots))
+
+    def submit(self, X, q0, n, ell, power, vel_kind, vel_params, dt, steps, method=LOCAL,
+               mode=DIRECT, precision=FP64, t0=0.0, centers=None, radius=0.0, weight=PU_WENDLAND):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        q = np.ascontiguousarray(np.asarray(q0, dtype=np.float64).reshape(X.shape[0], -1))
+        vp = (ctypes.c_double * 4)(*(list(np.asarray(vel_params, dtype=float)) + [0.0] * 4)[:4])
+        p = Problem(X.shape[0], X.ctypes.data, n, ell, float(power), mode, precision, vel_kind, vp,
+                    float(t0), float(dt), q.shape[1], q.ctypes.data)
+        C = None if centers is None else np.ascontiguousarray(centers, dtype=np.float64)
+        r = Request(method, p, steps, None if C is None else C.ctypes.data,
+                    0 if C is None else C.shape[0], float(radius), weight)
+        t = ctypes.c_uint64()
+        _check(load().rbfsl_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._shape[t.value] = (X.shape[0], q.shape[1])
+        return t.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int()
+        _check(load().rbfsl_server_poll(self._h, ticket, ctypes.byref(st)))
+        return st.value
+
+    def result(self, ticket):
+        N, T = self._shape.pop(ticket)
+        out = np.empty((N, T))
+        st = RequestStats()
+        _check(load().rbfsl_server_result(self._h, ticket, out.ctypes.data, ctypes.byref(st)))
+        return out, st
+
+    def wait_idle(self, timeout_s=600.0):
+        _check(load().rbfsl_server_wait_idle(self._h, float(timeout_s)))
+
+    def info(self) -> ServerInfo:
+        i = ServerInfo()
+        _check(load().rbfsl_server_info(self._h, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if self._h:
+            load().rbfsl_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
