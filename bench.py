@@ -302,7 +302,8 @@ def bench_served(rbfsl, precision, R=32, rate=200.0, seed=1804 * 100 + 5):
     th.start()
     th.join()
     srv.wait_idle(1200)
-    stats = [srv.result(tk)[1] for tk in tickets]
+    stats = [srv.result(tk, raise_on_failure=False)[1] for tk in tickets]
+    errors = sorted({s.message.decode() for s in stats if s.status != 0})
     info = srv.info()
     srv.close()
     lat = np.array([s.finish_s - s.submit_s for s in stats])
@@ -311,6 +312,7 @@ def bench_served(rbfsl, precision, R=32, rate=200.0, seed=1804 * 100 + 5):
     return {"requests": R, "arrival_rate_per_s": rate, "node_updates": int(nu),
             "value": nu / span, "wall_s": span, "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "failed": int(sum(s.status != 0 for s in stats)),
+            "errors": errors[:3],
             "peak_bytes": int(info.peak_bytes), "ticks": int(info.ticks)}
 
 

@@ -323,6 +323,7 @@ typedef struct rbfsl_request_stats {
     int64_t steps, node_updates;
     size_t device_bytes;                /* the admission estimate charged to the budget */
     int status;                         /* RBFSL_OK or the failure code */
+    char message[160];                  /* the failure's message ("" on success) */
 } rbfsl_request_stats;
 typedef struct rbfsl_server_info_t {
     int64_t ticks, queued;

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -82,10 +83,14 @@ __global__ void batch_trace_kernel(const BatchDesc *__restrict__ d, int np, int6
                         Xi[3 * j], Xi[3 * j + 1], Xi[3 * j + 2]);
 }
 
-// Shared memory of one point: system region (stencil_doubles), stencil (n int), weights
-// (n double), k-NN buffers (cap double + cap int + 1 int).
-__host__ __device__ inline int batch_point_doubles(int n, int m, int ld, int cap) {
-    return stencil_doubles(n, m, ld) + n + (n + 1) / 2 + cap + (cap + 2) / 2;
+// Shared memory of one point. Direct mode: system region (stencil_doubles), stencil (n int),
+// weights (n double), k-NN buffers (cap double + cap int + 1 int). Centre mode: right-hand
+// side and solution (2 m double), k-NN buffers.
+__host__ __device__ inline int batch_region_doubles(int mode, int n, int m, int ld) {
+    return mode == RBFSL_DIRECT ? stencil_doubles(n, m, ld) + (n + 1) / 2 + n : 2 * m;
+}
+__host__ __device__ inline int batch_point_doubles(int mode, int n, int m, int ld, int cap) {
+    return batch_region_doubles(mode, n, m, ld) + cap + (cap + 2) / 2;
 }
 
 // Gather-dot of one row from a point's weights (FP64 solution, rounded to FP32 in mixed
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
         const BatchDesc &b = d[p];
         if (!b.active) continue;
         const int n = b.n, m = b.m, ld = b.ld, cap = knn_cap(b.mode == RBFSL_DIRECT ? n : 1);
-        const int per = batch_point_doubles(n, m, ld, cap);
+        const int per = batch_point_doubles(b.mode, n, m, ld, cap);
         const int k = b.mode == RBFSL_DIRECT ? n : 1;
         if (b.ppt == 4 || b.mode == RBFSL_CENTER) {
             // one warp per point
@@ -132,9 +137,9 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             if (i >= b.N) continue;
             double *base = sm + (size_t)warp * per;
             double *A = base;
-            int32_t *S = reinterpret_cast<int32_t *>(base + stencil_doubles(n, m, ld));
-            double *wv = base + stencil_doubles(n, m, ld) + (n + 1) / 2;
-            double *bd = wv + n;
+            int32_t *S = reinterpret_cast<int32_t *>(base + stencil_doubles(n, m, ld));  // direct only
+            double *wv = base + stencil_doubles(n, m, ld) + (n + 1) / 2;                  // direct only
+            double *bd = base + batch_region_doubles(b.mode, n, m, ld);
             int *bi = reinterpret_cast<int *>(bd + cap);
             int *cnt = bi + cap;
             const double px = b.xi[3 * i], py = b.xi[3 * i + 1], pz = b.xi[3 * i + 2];
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             double *A = sm;
             int32_t *S = reinterpret_cast<int32_t *>(sm + stencil_doubles(n, m, ld));
             double *wv = sm + stencil_doubles(n, m, ld) + (n + 1) / 2;
-            double *bd = wv + n;
+            double *bd = sm + batch_region_doubles(b.mode, n, m, ld);
             int *bi = reinterpret_cast<int *>(bd + cap);
             int *cnt = bi + cap;
             const double px = b.xi[3 * i], py = b.xi[3 * i + 1], pz = b.xi[3 * i + 2];
@@ -291,7 +296,7 @@ int rebuild(rbfsl_batch *b) {
         nodes += d.N;
         tiles += d.ppt == 4 ? (d.N + 3) / 4 : d.N;
         const int cap = knn_cap(d.mode == RBFSL_DIRECT ? d.n : 1);
-        const int per = batch_point_doubles(d.n, d.m, d.ld, cap) * 8;
+        const int per = batch_point_doubles(d.mode, d.n, d.m, d.ld, cap) * 8;
         smem = std::max(smem, d.ppt == 4 ? 4 * per : per);
         b->slot_of[id] = (int)tab.size();
         tab.push_back(d);
@@ -315,6 +320,13 @@ int rebuild(rbfsl_batch *b) {
     b->total_tiles = tiles;
     b->smem = smem;
     if (smem > 0) {
+        int max_smem = 0;
+        RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+        if (smem > max_smem) {
+            set_error("batch: a problem's per-block shared memory (" + std::to_string(smem) +
+                      " bytes) exceeds the device limit");
+            return RBFSL_EINVAL;
+        }
         RBFSL_CUDA_TRY(cudaFuncSetAttribute(batch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         int per_sm = 0, sms = 0;
         RBFSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel, 128, smem));
@@ -610,7 +622,7 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
         int max_smem = 0;
         RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
         const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
-        const int per_bytes = batch_point_doubles(kn, km, (km + 1) | 1, knn_cap(kn)) * 8;
+        const int per_bytes = batch_point_doubles(RBFSL_DIRECT, kn, km, (km + 1) | 1, knn_cap(kn)) * 8;
         for (int ppt : {4, 1}) {
             if (ppt == 4 && 4 * per_bytes > max_smem) continue;  // four points do not fit on chip
             // only this class active, with the candidate tile shape

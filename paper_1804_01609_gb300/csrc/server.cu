@@ -9,6 +9,8 @@
 //      record the latency).
 // Node sets, stencil state and fields stay on the device between steps.
 #include <chrono>
+#include <cstdio>
+#include <string>
 #include <cmath>
 #include <condition_variable>
 #include <deque>
@@ -45,6 +47,7 @@ struct Req {
     int done_steps = 0;
     double t_submit = 0, t_admit = 0, t_finish = 0;
     std::vector<double> result;
+    std::string err;
 };
 
 // Device bytes a request holds while it runs (nodes, departure points, status, two fields,
@@ -158,6 +161,7 @@ void worker_loop(rbfsl_server *s) {
             r->t_admit = now_s(s);
             const int rc = start_request(s, *r);
             if (rc) {
+                r->err = std::string("admission: ") + (r->ctx ? rbfsl_last_error(r->ctx) : get_error());
                 release_request(s, *r);
                 std::lock_guard<std::mutex> lk(s->mu);
                 r->state = rc;
@@ -177,12 +181,24 @@ void worker_loop(rbfsl_server *s) {
         // one tick: every running request advances one SL step
         bool any_local = false;
         for (Req *r : active) {
-            if (r->method == RBFSL_LOCAL) any_local = true;
-            else if (rbfsl_step(r->ctx, 1) != RBFSL_OK) r->state = RBFSL_ECUDA;
+            if (r->method == RBFSL_LOCAL) {
+                any_local = true;
+            } else {
+                const int rc = rbfsl_step(r->ctx, 1);
+                if (rc != RBFSL_OK) {
+                    r->state = rc;
+                    r->err = std::string("step: ") + rbfsl_last_error(r->ctx);
+                }
+            }
         }
-        if (any_local && rbfsl_batch_step(s->batch, 1) != RBFSL_OK)
-            for (Req *r : active)
-                if (r->method == RBFSL_LOCAL) r->state = RBFSL_ECUDA;
+        if (any_local) {
+            const int rc = rbfsl_batch_step(s->batch, 1);
+            if (rc != RBFSL_OK) {
+                const std::string msg = std::string("batched step: ") + get_error();
+                for (Req *r : active)
+                    if (r->method == RBFSL_LOCAL) { r->state = rc; r->err = msg; }
+            }
+        }
         cudaStreamSynchronize(s->stream);
         for (Req *r : active)
             if (r->stream) cudaStreamSynchronize(r->stream);
@@ -195,7 +211,10 @@ void worker_loop(rbfsl_server *s) {
                 int rc;
                 if (r->method == RBFSL_LOCAL) rc = rbfsl_batch_get_q(s->batch, r->batch_id, r->result.data());
                 else rc = rbfsl_get_q(r->ctx, r->result.data(), RBFSL_F64, RBFSL_HOST);
-                if (rc) r->state = rc;
+                if (rc) {
+                    r->state = rc;
+                    r->err = std::string("result: ") + (r->ctx ? rbfsl_last_error(r->ctx) : get_error());
+                }
             }
             release_request(s, *r);
             std::lock_guard<std::mutex> lk(s->mu);
@@ -323,6 +342,7 @@ int rbfsl_server_result(rbfsl_server *s, uint64_t ticket, double *q_out, rbfsl_r
         st->node_updates = (int64_t)r->done_steps * r->prob.N;
         st->device_bytes = r->bytes;
         st->status = r->state == 2 ? RBFSL_OK : r->state;
+        std::snprintf(st->message, sizeof(st->message), "%s", r->err.c_str());
     }
     if (r->state != 2) {
         set_error("server_result: the request failed");

@@ -348,7 +348,7 @@ class RequestStats(ctypes.Structure):
     _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
                 ("finish_s", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("node_updates", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("message", ctypes.c_char * 160)]
 
 
 class ServerInfo(ctypes.Structure):
@@ -385,11 +385,17 @@ class Server:
         _check(load().rbfsl_server_poll(self._h, ticket, ctypes.byref(st)))
         return st.value
 
-    def result(self, ticket):
+    def result(self, ticket, raise_on_failure=True):
+        """(field, stats) of a finished request; (None, stats) for a failed one when
+        raise_on_failure is False."""
         N, T = self._shape.pop(ticket)
         out = np.empty((N, T))
         st = RequestStats()
-        _check(load().rbfsl_server_result(self._h, ticket, out.ctypes.data, ctypes.byref(st)))
+        rc = load().rbfsl_server_result(self._h, ticket, out.ctypes.data, ctypes.byref(st))
+        if rc != OK:
+            if raise_on_failure:
+                raise RbfslError(rc, st.message.decode() or "request failed")
+            return None, st
         return out, st
 
     def wait_idle(self, timeout_s=600.0):

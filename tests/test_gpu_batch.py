@@ -21,6 +21,7 @@ def _problems():
         (2562, 31, 2, 5, rbfsl.CENTER, rbfsl.FP64, 1, 2),
         (777, 55, 3, 7, rbfsl.CENTER, rbfsl.MIXED, 0, 4),
         (900, 84, 4, 9, rbfsl.DIRECT, rbfsl.MIXED, 1, 2),
+        (1200, 84, 4, 9, rbfsl.CENTER, rbfsl.FP64, 0, 2),
     ]
     out = []
     for k, (N, n, ell, p, mode, prec, vk, T) in enumerate(specs):
