@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
-    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace"],
+    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
     ap.add_argument("--repeat", type=int, default=3)
@@ -224,6 +224,44 @@ def cpu_baseline(w, budget_s=10.0):
                       f"gather of {w.T} tracers; FP64 C + OpenMP); {el:.1f} s"}
 
 
+# ----------------------------------------------------------------------------- W.q roofline
+def morton_order(X, bits=10):
+    """Node permutation along a 3-D Morton (Z-order) curve of the coordinates."""
+    q = np.clip(((X + 1.0) * 0.5 * (1 << bits)).astype(np.int64), 0, (1 << bits) - 1)
+    code = np.zeros(len(X), dtype=np.int64)
+    for b in range(bits):
+        for a in range(3):
+            code |= ((q[:, a] >> b) & 1) << (3 * b + a)
+    return np.argsort(code, kind="stable")
+
+
+def bench_wq_hbm(rbfsl, torch, stream, flush, K=10):
+    """The gather-dot W.q alone at a size where it is HBM-bound: N = 655,362 Morton-ordered
+    Fibonacci nodes, n = 84 nearest-node stencils, T = 16 tracers; FP32 (difference form) and
+    FP64. Algorithmic bytes per launch: N n (w + index) + 2 N T (read and write one row of q)."""
+    from paper_1804_01609_gb300 import inputs
+    N, n, T = 655362, 84, 16
+    X = inputs.nodes(N, 1804 * 100 + 6)
+    X = np.ascontiguousarray(X[morton_order(X)])
+    x = torch.as_tensor(X, device="cuda")
+    ix = rbfsl.rbfsl_knn_index_create(x, n, stream=stream)
+    I = torch.empty((N, n), dtype=torch.int32, device="cuda")
+    rbfsl.rbfsl_knn_query(ix, x, n, I, stream=stream)
+    ix.close()
+    g = torch.Generator(device="cuda").manual_seed(7)
+    out = {}
+    for name, dt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        with torch.cuda.stream(stream):
+            W = torch.rand((N, n), generator=g, device="cuda", dtype=torch.float64)
+            W = (W / W.sum(1, keepdim=True)).to(dt)
+            q = torch.rand((N, T), generator=g, device="cuda", dtype=torch.float64).to(dt)
+            qo = torch.empty_like(q)
+        ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I, W, q, qo, stream=stream), K, stream, flush, torch)
+        by = N * n * (es + 4) + 2 * N * T * es
+        out[name] = {"ms_per_launch": ms, "algorithmic_bytes": by, "achieved_gbs": by / (ms * 1e-3) / 1e9}
+    return out
+
+
 # ----------------------------------------------------------------------------- batched
 def bench_batched(rbfsl, torch, stream, precision, steps=2):
     """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
@@ -356,6 +394,12 @@ def run_case(args):
     """One kernel of the workload, on the first --nq departure points, --repeat times."""
     import torch
     from paper_1804_01609_gb300 import rbfsl
+    if args.case == "wq":
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(64 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        r = bench_wq_hbm(rbfsl, torch, stream, flush, K=args.repeat)
+        print(f"case wq: {json.dumps(r)}", flush=True)
+        return
     w = workload()
     N, n = w.N, w.n
     nq = min(args.nq, N)
@@ -369,6 +413,10 @@ def run_case(args):
     rbfsl.rbfsl_stencil_weights(x, I, n, w.ell, rbfsl.PHS, w.power, xi, W)
     q = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
     qo = torch.empty_like(q)
+    ctx = None
+    if args.case == "center":  # whole centre-stencil steps through the context
+        ctx = make_ctx(w, rbfsl.MIXED, torch.cuda.current_stream(), rbfsl, mode=rbfsl.CENTER)
+        ctx.step(1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -379,6 +427,8 @@ def run_case(args):
             rbfsl.rbfsl_gather_dot(I, W, q, qo)
         elif args.case == "knn":
             rbfsl.rbfsl_knn_query(ix, xi[:nq], n, I[:nq])
+        elif args.case == "center":
+            ctx.step(1)
         else:
             rbfsl.rbfsl_trace_rk4(x, w.vel_kind, w.vel_params, 0.3, w.dt, rbfsl.MIXED, xi)
     e1.record()
@@ -389,6 +439,8 @@ def run_case(args):
         m = n + (w.ell + 1) ** 2
         extra = f" {nq * weights_flops(m) / ms / 1e9:.3f} TFLOP/s ({nq} points, m={m})"
     print(f"case {args.case}: {ms:.3f} ms per launch{extra}", flush=True)
+    if ctx is not None:
+        ctx.close()
     ix.close()
 
 
@@ -504,6 +556,7 @@ def main():
             center["fp64"]["l2_vs_exact"] = rel_l2(qc64, q0)
             center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
+    wq = bench_wq_hbm(rbfsl, torch, stream, flush)
     batched = {}
     if not args.no_batched:
         batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),
@@ -545,11 +598,14 @@ def main():
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
                      "ms_per_launch": w_ms},
-        "roofline_gather": {"bound": "hbm", "kernel": "gather_dot_kernel<float>",
-                            "achieved": g_gbs, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-                            "frac": g_gbs / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
-                            "traffic": None, "ms_per_launch": g_ms,
-                            "note": "W and q fit in L2 at this N; see the N=655362 W.q measurement"},
+        "roofline_gather": {"bound": "hbm", "kernel": "gather_dot_vec_kernel<float, float4>",
+                            "workload": "N=655362 Morton-ordered nodes, n=84, T=16, FP32 difference form",
+                            "achieved": wq["f32"]["achieved_gbs"], "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                            "frac": wq["f32"]["achieved_gbs"] / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
+                            "traffic": None, "ms_per_launch": wq["f32"]["ms_per_launch"],
+                            "fp64": wq["f64"],
+                            "in_step_N40962_T32": {"achieved_gbs": g_gbs, "ms_per_launch": g_ms,
+                                                   "note": "W and q fit in L2 at this N"}},
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -52,9 +52,88 @@ __global__ void __launch_bounds__(256) gather_dot_kernel(const int32_t *__restri
     }
 }
 
+// Vectorised variant for T a multiple of the vector width V (4 floats or 2 doubles = 16 B):
+// a row group of G = T / V lanes serves one row (32 / G rows per warp), every lane owning V
+// consecutive tracers, so each gathered q row is read as G 16-byte pieces; (w, idx) come in
+// chunks of G, one per lane, and are broadcast by shuffles. Same summation order as the
+// scalar kernel (j ascending, one fma per term).
+template <typename R, typename RV, int V, bool kDiff>
+__global__ void __launch_bounds__(256) gather_dot_vec_kernel(const int32_t *__restrict__ idx,
+                                                             const R *__restrict__ W, int64_t Nq,
+                                                             int n, const R *__restrict__ q, int T,
+                                                             int G, R *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rows_per_warp = kWarp / G;
+    const int sub = lane % G, grp = lane / G;
+    const int64_t i = gwarp * rows_per_warp + grp;
+    const bool active = grp < rows_per_warp && i < Nq;
+    if (__all_sync(0xffffffffu, !active)) return;
+    const RV *qv = reinterpret_cast<const RV *>(q);
+    const int Tv = T / V;
+    R acc[V], qc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { acc[v] = R(0); qc[v] = R(0); }
+    if (kDiff && active) {
+        const int c = idx[i * n];
+        const RV x = c >= 0 ? qv[(int64_t)c * Tv + sub] : RV{};
+        const R *xr = reinterpret_cast<const R *>(&x);
+#pragma unroll
+        for (int v = 0; v < V; ++v) qc[v] = c >= 0 ? xr[v] : R(NAN);
+    }
+    for (int j0 = 0; j0 < n; j0 += G) {
+        R wj = R(0);
+        int sj = 0;
+        if (active && j0 + sub < n) {
+            wj = W[i * n + j0 + sub];
+            sj = idx[i * n + j0 + sub];
+        }
+        const int cnt = min(G, n - j0);
+        for (int jj = 0; jj < cnt; ++jj) {
+            const R w = __shfl_sync(0xffffffffu, wj, (lane / G) * G + jj);
+            const int s = __shfl_sync(0xffffffffu, sj, (lane / G) * G + jj);
+            if (active) {
+                const RV x = s >= 0 ? qv[(int64_t)s * Tv + sub] : RV{};
+                const R *xr = reinterpret_cast<const R *>(&x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const R val = s >= 0 ? xr[v] : R(NAN);
+                    acc[v] = fma(w, kDiff ? (val - qc[v]) : val, acc[v]);
+                }
+            }
+        }
+    }
+    if (active) {
+        RV o;
+        R *orr = reinterpret_cast<R *>(&o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) orr[v] = kDiff ? qc[v] + acc[v] : acc[v];
+        reinterpret_cast<RV *>(out)[i * Tv + sub] = o;
+    }
+}
+
 int launch_gather(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q, int T,
                   int dtype, void *q_out, cudaStream_t s) {
     if (Nq == 0) return RBFSL_OK;
+    const int V = dtype == RBFSL_F64 ? 2 : 4;
+    const bool aligned = ((uintptr_t)q % 16 == 0) && ((uintptr_t)q_out % 16 == 0);
+    if (T % V == 0 && T / V <= 32 && aligned) {
+        int G = 1;
+        while (G < T / V) G <<= 1;  // a power of two >= T / V lanes per row
+        if (G == T / V) {
+            const int rows_per_warp = kWarp / G;
+            const int threads = 256;
+            const int64_t warps = (Nq + rows_per_warp - 1) / rows_per_warp;
+            const unsigned blocks = (unsigned)((warps * kWarp + threads - 1) / threads);
+            if (dtype == RBFSL_F64)
+                gather_dot_vec_kernel<double, double2, 2, false><<<blocks, threads, 0, s>>>(
+                    idx, (const double *)w, Nq, n, (const double *)q, T, G, (double *)q_out);
+            else
+                gather_dot_vec_kernel<float, float4, 4, true><<<blocks, threads, 0, s>>>(
+                    idx, (const float *)w, Nq, n, (const float *)q, T, G, (float *)q_out);
+            return launch_status("gather_dot_vec");
+        }
+    }
     int L = 1;
     while (L < T && L < 32) L <<= 1;
     const int rows_per_warp = kWarp / L;
