@@ -284,7 +284,7 @@ int prepare(rbfsl_ctx *c) {
         CTX_TRY(c, cudaMemcpy(d_lo, lo.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice));
         CTX_TRY(c, cudaMemsetAsync(d_bad, 0, sizeof(int32_t), c->stream));
         rc = launch_stencil_factor(c->X, d_ms, c->Ik, d_lo, N, (int)n, (ell + 1) * (ell + 1), ell, pw,
-                                   c->LU, c->perm, d_bad, c->stream);
+                                   c->LU, c->perm, d_bad, c->stream, 1);
         int32_t bad = 0;
         if (rc == RBFSL_OK) {
             cudaError_t e = cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);

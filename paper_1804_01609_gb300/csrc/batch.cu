@@ -478,7 +478,7 @@ int rbfsl_batch_add(rbfsl_batch *b, const rbfsl_problem *pr, int *id_out) {
         cudaMemcpyAsync(d_ms, ms.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(d_lo, lo.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
-        rc = launch_stencil_factor(h.X, d_ms, h.Ik, d_lo, N, (int)n, M, pr->ell, pw, h.LU, h.perm, d_bad, s);
+        rc = launch_stencil_factor(h.X, d_ms, h.Ik, d_lo, N, (int)n, M, pr->ell, pw, h.LU, h.perm, d_bad, s, 1);
         int32_t bad = 0;
         if (rc == RBFSL_OK && (cudaMemcpyAsync(&bad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                                cudaStreamSynchronize(s) != cudaSuccess)) {

@@ -358,14 +358,18 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
 }
 
 // Centre-stencil weights of one point by one warp (Sec. 3.3): the point uses the stencil
-// S = Ik[k] of its nearest node k, whose m x m saddle-point matrix was factorised once
-// (row-major LU F, row order pr). b = [phi(|p - x_Sj|); Y(p)], then L U w~ = P b with row-wise
-// dot products (lanes over a contiguous factor row, warp-shuffle sums). b and y: 2 m shared
-// doubles of the warp. On return y[0..n) holds the weights (all lanes).
-__device__ __forceinline__ void center_point(const double *__restrict__ X, const int32_t *__restrict__ S,
-                                             const double *__restrict__ F, const int32_t *__restrict__ pr,
-                                             int n, int m, int ell, int half, double px, double py,
-                                             double pz, double *b, double *y, int lane) {
+// S = Ik[k] of its nearest node k, whose m x m saddle-point matrix was factorised once. Ft is
+// that factor stored column-major with its diagonal replaced by the reciprocal (Ft[c m + r] =
+// L_rc or U_rc, Ft[c m + c] = 1 / U_cc), pr its row order. b = [phi(|p - x_Sj|); Y(p)], then
+// L U w~ = P b by column-oriented substitution: lane l keeps rows l, l+32, ... of the
+// right-hand side in registers; after row c is final it is broadcast by a shuffle and every lane
+// updates its later (earlier) rows with one coalesced column of the factor. b: m shared
+// doubles of the warp. On return y_out[0..n) (shared, m doubles) holds the weights.
+template <int NU>
+__device__ __forceinline__ void center_point_nu(const double *__restrict__ X, const int32_t *__restrict__ S,
+                                                const double *__restrict__ Ft, const int32_t *__restrict__ pr,
+                                                int n, int m, int ell, int half, double px, double py,
+                                                double pz, double *b, double *y_out, int lane) {
     for (int j = lane; j < n; j += 32) {
         const int64_t s = S[j];
         const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
@@ -373,24 +377,63 @@ __device__ __forceinline__ void center_point(const double *__restrict__ X, const
     }
     if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { b[n + c] = v; });
     __syncwarp();
-    for (int r = lane; r < m; r += 32) y[r] = b[pr[r]];
+    double y[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int r = lane + 32 * u;
+        y[u] = r < m ? b[pr[r]] : 0.0;
+    }
+    // forward: unit lower
+    for (int c = 0; c < m - 1; ++c) {
+        const int uc = c >> 5;
+        double own = 0.0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if (u == uc) own = y[u];
+        const double yc = __shfl_sync(0xffffffffu, own, c & 31);
+        const double *col = Ft + (size_t)c * m;
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (u >= ((c + 1) >> 5)) {  // warp-uniform: no FP64 issue for finished chunks
+                const int r = lane + 32 * u;
+                if (r > c && r < m) y[u] = fma(-col[r], yc, y[u]);
+            }
+        }
+    }
+    // backward: upper, reciprocal diagonal
+    for (int c = m - 1; c >= 0; --c) {
+        const int uc = c >> 5;
+        const double *col = Ft + (size_t)c * m;
+        double own = 0.0;
+#pragma unroll
+        for (int u = 0; u < NU; ++u)
+            if (u == uc) own = y[u];
+        const double xc = __shfl_sync(0xffffffffu, own, c & 31) * col[c];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (u == uc && lane == (c & 31)) y[u] = xc;
+            if (u <= ((c - 1) >> 5) && c > 0) {
+                const int r = lane + 32 * u;
+                if (r < c) y[u] = fma(-col[r], xc, y[u]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int r = lane + 32 * u;
+        if (r < m) y_out[r] = y[u];
+    }
     __syncwarp();
-    for (int r = 1; r < m; ++r) {  // forward: y_r -= sum_{c<r} L_rc y_c (unit lower)
-        double s = 0.0;
-        for (int c = lane; c < r; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[r] -= s;
-        __syncwarp();
-    }
-    for (int r = m - 1; r >= 0; --r) {  // backward: y_r = (y_r - sum_{c>r} U_rc y_c) / U_rr
-        double s = 0.0;
-        for (int c = r + 1 + lane; c < m; c += 32) s = fma(F[(size_t)r * m + c], y[c], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[r] = (y[r] - s) / F[(size_t)r * m + r];
-        __syncwarp();
-    }
+}
+
+__device__ __forceinline__ void center_point(const double *__restrict__ X, const int32_t *__restrict__ S,
+                                             const double *__restrict__ Ft, const int32_t *__restrict__ pr,
+                                             int n, int m, int ell, int half, double px, double py,
+                                             double pz, double *b, double *y, int lane) {
+    if (m <= 64) center_point_nu<2>(X, S, Ft, pr, n, m, ell, half, px, py, pz, b, y, lane);
+    else if (m <= 96) center_point_nu<3>(X, S, Ft, pr, n, m, ell, half, px, py, pz, b, y, lane);
+    else if (m <= 128) center_point_nu<4>(X, S, Ft, pr, n, m, ell, half, px, py, pz, b, y, lane);
+    else center_point_nu<5>(X, S, Ft, pr, n, m, ell, half, px, py, pz, b, y, lane);
 }
 
 // One output row of the gather-dot for tracer lanes t = lane, lane + 32, ... < T, with the

@@ -91,7 +91,8 @@ int sh_tables_init();
 
 int launch_stencil_factor(const double *X, const int64_t *mstart, const int32_t *members,
                           const int64_t *lu_off, int64_t count, int max_n, int M, int ell,
-                          int power, double *LU, int32_t *perm, int32_t *status, cudaStream_t s);
+                          int power, double *LU, int32_t *perm, int32_t *status, cudaStream_t s,
+                          int colmajor);
 int launch_center_weights(const double *X, const int32_t *K, const int32_t *Ik, const double *LU,
                           const int32_t *perm, int64_t Nq, int n, int ell, int power,
                           const double *p, int32_t *I, void *w, int w_dtype, int32_t *status,

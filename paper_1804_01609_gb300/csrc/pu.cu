@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(128) pu_factor_kernel(const double *__restrict
                                                         const int64_t *__restrict__ lu_off, int M,
                                                         int ell, int half, double *__restrict__ LU,
                                                         int32_t *__restrict__ perm,
-                                                        int32_t *__restrict__ status) {
+                                                        int32_t *__restrict__ status, int colmajor) {
     extern __shared__ double sm[];
     __shared__ int s_p, s_bad;
     __shared__ int order[RBFSL_MAX_SYSTEM];
@@ -165,7 +165,14 @@ __global__ void __launch_bounds__(128) pu_factor_kernel(const double *__restrict
         return;
     }
     double *out = LU + lu_off[l];
-    for (int e = t; e < m * m; e += 128) out[e] = A[(e / m) * ld + e % m];
+    if (!colmajor) {
+        for (int e = t; e < m * m; e += 128) out[e] = A[(e / m) * ld + e % m];
+    } else {  // column-major, diagonal replaced by its reciprocal (centre stencils)
+        for (int e = t; e < m * m; e += 128) {
+            const int c = e / m, r = e % m;
+            out[e] = r == c ? 1.0 / A[r * ld + c] : A[r * ld + c];
+        }
+    }
     int32_t *pr = perm + mstart[l] + l * M;
     for (int i = t; i < m; i += 128) pr[i] = order[i];
 }
@@ -316,14 +323,15 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
 // method's centre stencils). Dynamic shared memory sized for the largest system.
 int launch_stencil_factor(const double *X, const int64_t *mstart, const int32_t *members,
                           const int64_t *lu_off, int64_t count, int max_n, int M, int ell,
-                          int power, double *LU, int32_t *perm, int32_t *status, cudaStream_t s) {
+                          int power, double *LU, int32_t *perm, int32_t *status, cudaStream_t s,
+                          int colmajor) {
     int rc = sh_tables_init();
     if (rc) return rc;
     const int mmax = max_n + M;
     const int smem = ((mmax * (mmax | 1)) + 3 * max_n) * (int)sizeof(double);
     RBFSL_CUDA_TRY(cudaFuncSetAttribute(pu_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     pu_factor_kernel<<<(unsigned)count, 128, smem, s>>>(X, mstart, members, lu_off, M, ell, (power - 1) / 2,
-                                                        LU, perm, status);
+                                                        LU, perm, status, colmajor);
     return launch_status("stencil_factor");
 }
 
@@ -405,7 +413,7 @@ int pu_build(rbfsl_pu *u, const double *x, int64_t N, const double *centers, int
     RBFSL_CUDA_TRY(cudaMemsetAsync(u->status, 0, sizeof(int32_t), s));
     pu_members_kernel<<<blocks, 128, 0, s>>>(grid_view(u->nodes_ix), u->centers, Mp, R, nullptr, u->mstart, u->members);
     if ((rc = launch_stencil_factor(u->X, u->mstart, u->members, u->lu_off, Mp, u->max_members, u->M, ell,
-                                    power, u->LU, u->perm, u->status, s)))
+                                    power, u->LU, u->perm, u->status, s, 0)))
         return rc;
     int32_t bad = 0;
     RBFSL_CUDA_TRY(cudaMemcpyAsync(&bad, u->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
