@@ -262,6 +262,43 @@ def bench_wq_hbm(rbfsl, torch, stream, flush, K=10):
     return out
 
 
+# ----------------------------------------------------------------------------- global RBF
+def bench_global(rbfsl, torch, stream, flush, K=3, accuracy_steps=200):
+    """Global Gaussian RBF (eps = 6), N = 10,242, 64 smooth tracers, tilted rotation: one-time
+    FP64 LU, then per step an FP64 solve and the evaluation at the departure points (FP64, or
+    FP32 in mixed precision). Errors after one revolution (200 steps) against the exact
+    solution (the initial field)."""
+    from paper_1804_01609_gb300 import inputs
+    w = inputs.config_global_rotation()
+    out = {}
+    for prec, name in ((rbfsl.FP64, "fp64"), (rbfsl.MIXED, "mixed")):
+        ctx = rbfsl.Context(0, stream=stream)
+        ctx.set_nodes(w.X)
+        ctx.set_velocity(w.vel_kind, w.vel_params)
+        ctx.set_method(rbfsl.GLOBAL)
+        ctx.set_kernel(rbfsl.GAUSS, w.eps)
+        ctx.set_precision(prec)
+        ctx.set_dt(w.dt)
+        q0 = w.q0()
+        ctx.set_tracers(q0 if prec == rbfsl.FP64 else q0.astype(np.float32))
+        t0 = time.perf_counter()
+        ctx.step(1)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        ms = timed_steps(ctx, K, 1, stream, flush, torch)
+        r = {"value": w.N / (float(ms.mean()) / 1e3), "ms_per_step": float(ms.mean()),
+             "setup_and_first_step_s": setup}
+        if accuracy_steps:
+            done = 2 + K
+            ctx.step(w.steps - done)
+            q = ctx.get_q()
+            r["l2_vs_exact"] = rel_l2(q, q0)
+            r["linf_vs_exact"] = rel_linf(q, q0)
+        ctx.close()
+        out[name] = r
+    return out
+
+
 # ----------------------------------------------------------------------------- batched
 def bench_batched(rbfsl, torch, stream, precision, steps=2):
     """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
@@ -557,6 +594,7 @@ def main():
             center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
     wq = bench_wq_hbm(rbfsl, torch, stream, flush)
+    glob = bench_global(rbfsl, torch, stream, flush)
     batched = {}
     if not args.no_batched:
         batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),
@@ -586,6 +624,7 @@ def main():
                             "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
         "center_stencils": center,
+        "global_N10242_T64": glob,
         "batched_64_problems": batched,
         "served": served,
         "accuracy": acc,

@@ -383,40 +383,65 @@ __device__ __forceinline__ void center_point_nu(const double *__restrict__ X, co
         const int r = lane + 32 * u;
         y[u] = r < m ? b[pr[r]] : 0.0;
     }
+    // Column c's live entries (rows > c forward, rows < c backward) are loaded two columns
+    // ahead into registers, so HBM latency overlaps the substitution.
+    auto load_lower = [&](int c, double *v) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int r = lane + 32 * u;
+            v[u] = (c < m - 1 && u >= ((c + 1) >> 5) && r > c && r < m) ? Ft[(size_t)c * m + r] : 0.0;
+        }
+    };
+    auto load_upper = [&](int c, double *v) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int r = lane + 32 * u;
+            v[u] = (c >= 0 && u <= (c >> 5) && r <= c) ? Ft[(size_t)c * m + r] : 0.0;
+        }
+    };
+    double c0[NU], c1[NU], c2[NU];
     // forward: unit lower
+    load_lower(0, c0);
+    load_lower(1, c1);
     for (int c = 0; c < m - 1; ++c) {
+        load_lower(c + 2, c2);
         const int uc = c >> 5;
         double own = 0.0;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
             if (u == uc) own = y[u];
         const double yc = __shfl_sync(0xffffffffu, own, c & 31);
-        const double *col = Ft + (size_t)c * m;
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
             if (u >= ((c + 1) >> 5)) {  // warp-uniform: no FP64 issue for finished chunks
                 const int r = lane + 32 * u;
-                if (r > c && r < m) y[u] = fma(-col[r], yc, y[u]);
+                if (r > c && r < m) y[u] = fma(-c0[u], yc, y[u]);
             }
         }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) { c0[u] = c1[u]; c1[u] = c2[u]; }
     }
-    // backward: upper, reciprocal diagonal
+    // backward: upper, reciprocal diagonal (the diagonal entry of column c is its row c)
+    load_upper(m - 1, c0);
+    load_upper(m - 2, c1);
     for (int c = m - 1; c >= 0; --c) {
+        load_upper(c - 2, c2);
         const int uc = c >> 5;
-        const double *col = Ft + (size_t)c * m;
-        double own = 0.0;
+        double own = 0.0, dinv = 0.0;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
-            if (u == uc) own = y[u];
-        const double xc = __shfl_sync(0xffffffffu, own, c & 31) * col[c];
+            if (u == uc) { own = y[u]; dinv = c0[u]; }
+        const double xc = __shfl_sync(0xffffffffu, own, c & 31) * __shfl_sync(0xffffffffu, dinv, c & 31);
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
             if (u == uc && lane == (c & 31)) y[u] = xc;
             if (u <= ((c - 1) >> 5) && c > 0) {
                 const int r = lane + 32 * u;
-                if (r < c) y[u] = fma(-col[r], xc, y[u]);
+                if (r < c) y[u] = fma(-c0[u], xc, y[u]);
             }
         }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) { c0[u] = c1[u]; c1[u] = c2[u]; }
     }
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
