@@ -73,7 +73,7 @@ enum { RBFSL_FP64 = 0, RBFSL_MIXED = 1 };
 enum { RBFSL_F64 = 0, RBFSL_F32 = 1 };    /* element types of caller buffers */
 enum { RBFSL_HOST = 0, RBFSL_DEVICE = 1 }; /* where a caller buffer lives */
 
-/* Limits of this build. */
+/* Limits of this library. */
 #define RBFSL_MAX_SH_DEGREE 8     /* ell <= 8, (ell+1)^2 <= 81 harmonics */
 #define RBFSL_MAX_SYSTEM 160      /* n + (ell+1)^2 <= 160 for one saddle-point system */
 #define RBFSL_MAX_K 256           /* neighbours per k-NN query */

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
         }
     });
     __syncwarp();
-    if (cnt[warp] > kPuMaxPatches) {  // more overlapping patches than this build gathers
+    if (cnt[warp] > kPuMaxPatches) {  // more overlapping patches than the kernel gathers
         for (int c = lane; c < T; c += 32) out[i * T + c] = (R)NAN;
         if (status && lane == 0) status[i] = RBFSL_EINVAL;
         return;

@@ -76,7 +76,7 @@ def test_eval_parity(orc, N, T):
 
 
 def test_cfg3_full_size_factor_and_step(orc):
-    """BASELINE config 3 at full size: N=10242, Gaussian eps=6, 64 tracers. Residual of the
+    """The global workload at full size: N=10242, Gaussian eps=6, 64 tracers. Residual of the
     GPU factor on sampled rows, one evaluation checked on sampled points against the oracle."""
     w = inputs.config_global_rotation()
     X, Q = w.X, w.q0()

@@ -4,7 +4,7 @@ Tolerances (FP64 unless stated):
   departure points        1e-14 absolute (RK4 with the same stage order; rounding only)
   mixed departure points  5e-8 absolute (FP32 stages, displacement ~ omega dt)
   k-NN                    bit-exact indices vs brute force on the same points
-  weights, n=31 ell=2     1e-10 relative to max|w| (the benchmark spec's bound; FP64 weights are
+  weights, n=31 ell=2     1e-10 relative to max|w| (the workload's stated bound; FP64 weights are
                           determined to ~3e-13 at this size)
   weights, n=84 ell=4     the saddle-point systems have cond ~1e18: moving the nodes by one
                           ulp changes the weights by ~1e-6..1e-3, so two FP64 solvers cannot
@@ -202,7 +202,7 @@ def _run_ctx(w, precision=rbfsl.FP64, mode=rbfsl.DIRECT, steps=None):
 
 @pytest.mark.parametrize("mode", [rbfsl.DIRECT, rbfsl.CENTER])
 def test_cfg1_full_run_matches_oracle(orc, cfg1, mode):
-    """BASELINE config 1 at full size: N=2562, n=31, r^3, ell=2, one revolution in 120 steps."""
+    """The rotation workload at full size: N=2562, n=31, r^3, ell=2, one revolution in 120 steps."""
     q, st = _run_ctx(cfg1, mode=mode)
     assert st.singular_points == 0 and st.knn_failures == 0
     ref = orc.local_run(cfg1.X, cfg1.q0(), cfg1.n, cfg1.ell, cfg1.power, cfg1.vel_kind,
@@ -222,7 +222,7 @@ def test_cfg1_mixed_precision_error(orc, cfg1):
 
 
 def test_cfg2_full_size_sampled_step(orc, cfg2):
-    """BASELINE config 2 at full size (N=40962, n=84, r^5, ell=4, 33 tracers): two FP64 steps
+    """The deformation workload at full size (N=40962, n=84, r^9, ell=4, 32 tracers): two FP64 steps
     through the context; the second step's stencils, weights and outputs are checked on sampled
     rows against the oracle given the same departure points and input field."""
     w = cfg2
