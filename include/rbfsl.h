@@ -203,6 +203,19 @@ int rbfsl_pu_destroy(rbfsl_pu *pu);
 int rbfsl_pu_apply(rbfsl_pu *pu, const double *q, int T, const double *p, int64_t Nq,
                    int weight_kind, int dtype, void *out, int32_t *status, void *stream);
 
+/* Global-interpolant evaluation on the tensor cores (tcgen05): the same sum as
+ * rbfsl_global_eval, with the kernel values computed in FP32 and both operands split into a
+ * TF32 high part and an FP32 remainder; hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor
+ * memory (the mixed-precision evaluation). c: device N x T of c_dtype (RBFSL_F64 or RBFSL_F32);
+ * out: device Nq x T FP32. workspace: device buffer of at least
+ * rbfsl_global_eval_tc_workspace_bytes(N, T) bytes, 16-byte aligned (the split, transposed
+ * coefficients and an error word); the caller owns it and must not share it between calls
+ * that overlap on the GPU. Errors: EINVAL, ECUDA. */
+size_t rbfsl_global_eval_tc_workspace_bytes(int64_t N, int T);
+int rbfsl_global_eval_tc(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
+                         double eps, const void *c, int c_dtype, int T, float *out,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
 /* ================================================================== context (Algorithm 1) */
 typedef struct rbfsl_ctx rbfsl_ctx;
 

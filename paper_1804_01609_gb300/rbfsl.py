@@ -63,6 +63,8 @@ SIGNATURES = {
     "rbfsl_global_factor_noalloc": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
+    "rbfsl_global_eval_tc_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
+    "rbfsl_global_eval_tc": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P, ctypes.c_size_t, _P]),
     "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
     "rbfsl_pu_destroy": (_I, [_P]),
     "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
@@ -416,6 +418,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def rbfsl_global_eval_tc(p, x, kernel, eps, c, out, workspace=None, stream=None):
+    """Tensor-core (split TF32) evaluation; workspace: a uint8 device tensor (allocated here
+    when None)."""
+    import torch
+    T = c.shape[1] if c.dim() == 2 else 1
+    need = load().rbfsl_global_eval_tc_workspace_bytes(x.shape[0], T)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=c.device)
+    _check(load().rbfsl_global_eval_tc(_ptr(p), p.shape[0], _ptr(x), x.shape[0], kernel, float(eps),
+                                       _ptr(c), _dtype_code(c), T, _ptr(out), _ptr(workspace),
+                                       workspace.numel(), _stream(stream)))
+    return workspace
 
 
 # --------------------------------------------------------------------------- context
