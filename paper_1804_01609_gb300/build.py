@@ -1,6 +1,7 @@
 """Build the CUDA library librbfsl.so in-tree for sm_103a (GB300).
 
-Every .cu under csrc/ is compiled in parallel with relocatable device code and linked by
+Every .cu under csrc/ is compiled in parallel (with relocatable device code, except the units in
+WHOLE_PROGRAM) and linked by
 nvcc into paper_1804_01609_gb300/_build/librbfsl.so. Rebuilds only when a source or header
 is newer than the library.
 """
@@ -20,6 +21,11 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbfsl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Translation units compiled as whole programs (no relocatable device code). global_tc.cu
+# references no device symbol of another unit; built with -rdc=true, its tcgen05 kernel returned
+# wrong accumulators on sm_103a (a standalone build of the same source reproduces this), built
+# whole-program it matches the FP64 evaluation to the split-TF32 bound.
+WHOLE_PROGRAM = {"global_tc.cu"}
 
 
 def nvcc() -> str:
@@ -57,7 +63,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc] + common + ["-c", src, "-o", obj]
+        flags = common
+        if os.path.basename(src) in WHOLE_PROGRAM:
+            flags = [f for f in common if f != "-rdc=true"]
+        cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

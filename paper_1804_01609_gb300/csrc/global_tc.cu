@@ -19,6 +19,7 @@ namespace rbfsl {
 constexpr int kTcM = 128, kTcN = 32, kTcK = 32;  // block tile: points x tracers x node chunk
 constexpr int kTcStageFloats = 2 * kTcM * kTcK + 2 * kTcN * kTcK;  // Ahi, Alo, Bhi, Blo
 constexpr long long kTcWaitLimit = 1LL << 22;
+constexpr uint32_t kTcLbo = 128, kTcSbo = (kTcK / 4) * 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(128) global_eval_tc_kernel(const double *__res
                                                              const float *__restrict__ Chi,
                                                              const float *__restrict__ Clo, int64_t Npad,
                                                              int T, float *__restrict__ out,
-                                                             int32_t *__restrict__ err) {
+                                                             int32_t *__restrict__ err, uint32_t lbo,
+                                                             uint32_t sbo) {
     extern __shared__ __align__(1024) float tsm[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t s_tmem;
@@ -167,8 +169,6 @@ __global__ void __launch_bounds__(128) global_eval_tc_kernel(const double *__res
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo), b_hi = smem_u32(Bhi), b_lo = smem_u32(Blo);
-            // LBO: next core matrix along K (128 B); SBO: next 8-row group (8 core matrices)
-            const uint32_t lbo = 128, sbo = (kTcK / 4) * 128;
 #pragma unroll
             for (int ks = 0; ks < kTcK / 8; ++ks) {
                 const uint32_t koff = ks * 2 * 128;  // two core matrices (8 TF32) per k-step
@@ -239,7 +239,9 @@ int launch_global_eval_tc(const double *P, int64_t Nq, const double *X, int64_t 
     const int smem = 2 * kTcStageFloats * (int)sizeof(float);
     RBFSL_CUDA_TRY(cudaFuncSetAttribute(global_eval_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((unsigned)((Nq + kTcM - 1) / kTcM), (unsigned)(Tpad / kTcN));
-    global_eval_tc_kernel<<<grid, 128, smem, s>>>(P, Nq, X, N, kind, (float)(eps * eps), hi, lo, Npad, T, out, err);
+    // LBO: byte step between core matrices along K; SBO: byte step between 8-row groups
+    global_eval_tc_kernel<<<grid, 128, smem, s>>>(P, Nq, X, N, kind, (float)(eps * eps), hi, lo, Npad, T, out, err,
+                                                  kTcLbo, kTcSbo);
     return launch_status("global_eval_tc");
 }
 

@@ -1,7 +1,8 @@
 """Tensor-core (tcgen05, split TF32) evaluation of the global interpolant against the FP64
 oracle. Tolerance: split TF32 keeps ~21 bits of each factor and the three products accumulate
-in FP32, so the error is a few 1e-7 of the sum's scale sum_j |phi_ij c_j|; bound 2e-6 of it,
-the same as the FP32 CUDA-core evaluation."""
+in FP32 (a few 1e-7 of the sum's scale sum_j |phi_ij c_j|); the kernel values come from FP32
+squared distances, whose rounding (~1e-7 of d^2 <= 4) is amplified by eps^2 = 36 in the
+exponent. Bound: 1e-5 of the scale."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,7 @@ def test_tc_eval_parity(orc, Nq, N, T):
     rbfsl.rbfsl_global_eval_tc(_t(P), _t(X), rbfsl.GAUSS, EPS, _t(C), out)
     got = out.cpu().numpy().astype(np.float64)
     assert np.isfinite(got).all()
-    assert np.all(np.abs(got - ref) <= 2e-6 * scale + 1e-30)
+    assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-30)
 
 
 def test_tc_eval_full_size_sampled(orc):
@@ -48,4 +49,4 @@ def test_tc_eval_full_size_sampled(orc):
     C32 = C.astype(np.float32).astype(np.float64)
     ref = orc.global_eval(Xi[rows], w.X, C32, orc.GAUSS, EPS)
     scale = np.exp(-(EPS ** 2) * ((Xi[rows][:, None, :] - w.X[None]) ** 2).sum(-1)) @ np.abs(C32)
-    assert np.all(np.abs(out.cpu().numpy()[rows] - ref) <= 2e-6 * scale)
+    assert np.all(np.abs(out.cpu().numpy()[rows] - ref) <= 1e-5 * scale)
