@@ -151,8 +151,7 @@ def make_ctx(w, precision, stream, rbfsl, mode=None):
     ctx.set_precision(precision)
     ctx.set_dt(w.dt)
     ctx.set_time(0.0)
-    q0 = w.q0()
-    ctx.set_tracers(q0.astype(np.float32) if precision == rbfsl.MIXED else q0)
+    ctx.set_tracers(w.q0())  # FP64 field; the mixed step keeps it as FP32 pairs
     return ctx
 
 
@@ -235,10 +234,23 @@ def morton_order(X, bits=10):
     return np.argsort(code, kind="stable")
 
 
+def pairs_of(a):
+    """FP64 array -> FP32 pairs (hi, lo) in a trailing axis of 2, as the mixed step stores q."""
+    hi = a.astype(np.float32)
+    return np.ascontiguousarray(np.stack([hi, (a - hi.astype(np.float64)).astype(np.float32)], axis=-1))
+
+
+def pairs_of_t(t):
+    import torch
+    hi = t.to(torch.float32)
+    return torch.stack([hi, (t - hi.to(torch.float64)).to(torch.float32)], dim=-1).contiguous()
+
+
 def bench_wq_hbm(rbfsl, torch, stream, flush, K=10):
     """The gather-dot W.q alone at a size where it is HBM-bound: N = 655,362 Morton-ordered
-    Fibonacci nodes, n = 84 nearest-node stencils, T = 16 tracers; FP32 (difference form) and
-    FP64. Algorithmic bytes per launch: N n (w + index) + 2 N T (read and write one row of q)."""
+    Fibonacci nodes, n = 84 nearest-node stencils, T = 16 tracers; FP32 (difference form), FP64
+    and FP32 pairs (the mixed step's storage and arithmetic). Algorithmic bytes per launch:
+    N n (w + index) + 2 N T (read and write one row of q)."""
     from paper_1804_01609_gb300 import inputs
     N, n, T = 655362, 84, 16
     X = inputs.nodes(N, 1804 * 100 + 6)
@@ -250,13 +262,18 @@ def bench_wq_hbm(rbfsl, torch, stream, flush, K=10):
     ix.close()
     g = torch.Generator(device="cuda").manual_seed(7)
     out = {}
-    for name, dt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+    for name, dt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8), ("f32x2", None, 8)):
         with torch.cuda.stream(stream):
             W = torch.rand((N, n), generator=g, device="cuda", dtype=torch.float64)
-            W = (W / W.sum(1, keepdim=True)).to(dt)
-            q = torch.rand((N, T), generator=g, device="cuda", dtype=torch.float64).to(dt)
+            W = W / W.sum(1, keepdim=True)
+            q = torch.rand((N, T), generator=g, device="cuda", dtype=torch.float64)
+            if dt is None:  # FP32 pairs (the mixed-precision storage)
+                W, q = pairs_of_t(W), pairs_of_t(q)
+            else:
+                W, q = W.to(dt), q.to(dt)
             qo = torch.empty_like(q)
-        ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I, W, q, qo, stream=stream), K, stream, flush, torch)
+        ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I, W, q, qo, stream=stream, pairs=dt is None), K, stream,
+                     flush, torch)
         by = N * n * (es + 4) + 2 * N * T * es
         out[name] = {"ms_per_launch": ms, "algorithmic_bytes": by, "achieved_gbs": by / (ms * 1e-3) / 1e9}
     return out
@@ -280,7 +297,7 @@ def bench_global(rbfsl, torch, stream, flush, K=3, accuracy_steps=200):
         ctx.set_precision(prec)
         ctx.set_dt(w.dt)
         q0 = w.q0()
-        ctx.set_tracers(q0 if prec == rbfsl.FP64 else q0.astype(np.float32))
+        ctx.set_tracers(q0)
         t0 = time.perf_counter()
         ctx.step(1)
         torch.cuda.synchronize()
@@ -446,9 +463,9 @@ def run_case(args):
     ix = rbfsl.rbfsl_knn_index_create(x, n)
     I = torch.empty((N, n), dtype=torch.int32, device="cuda")
     rbfsl.rbfsl_knn_query(ix, xi, n, I)
-    W = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    W = torch.empty((N, n, 2), dtype=torch.float32, device="cuda")  # FP32 pairs, as the mixed step
     rbfsl.rbfsl_stencil_weights(x, I, n, w.ell, rbfsl.PHS, w.power, xi, W)
-    q = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
+    q = torch.as_tensor(pairs_of(w.q0()), device="cuda")
     qo = torch.empty_like(q)
     ctx = None
     if args.case == "center":  # whole centre-stencil steps through the context
@@ -461,7 +478,7 @@ def run_case(args):
         if args.case == "weights":
             rbfsl.rbfsl_stencil_weights(x, I[:nq], n, w.ell, rbfsl.PHS, w.power, xi[:nq], W[:nq])
         elif args.case == "gather":
-            rbfsl.rbfsl_gather_dot(I, W, q, qo)
+            rbfsl.rbfsl_gather_dot(I, W, q, qo, pairs=True)
         elif args.case == "knn":
             rbfsl.rbfsl_knn_query(ix, xi[:nq], n, I[:nq])
         elif args.case == "center":
@@ -522,14 +539,14 @@ def main():
     # dominant kernel (FP64 stencil solve) and the gather-dot, timed alone on the same stream
     xi_t, I_t, _ = ctx.last_step_tensors(n, torch.float32)
     x_t = torch.as_tensor(w.X, device="cuda")
-    w32 = torch.empty((N, n), dtype=torch.float32, device="cuda")
-    rbfsl.rbfsl_stencil_weights(x_t, I_t, n, w.ell, rbfsl.PHS, w.power, xi_t, w32, stream=stream)
+    wp = torch.empty((N, n, 2), dtype=torch.float32, device="cuda")  # FP32 pairs, as the step stores them
+    rbfsl.rbfsl_stencil_weights(x_t, I_t, n, w.ell, rbfsl.PHS, w.power, xi_t, wp, stream=stream)
     w_ms = time_op(lambda: rbfsl.rbfsl_stencil_weights(x_t, I_t, n, w.ell, rbfsl.PHS, w.power,
-                                                       xi_t, w32, stream=stream),
+                                                       xi_t, wp, stream=stream),
                    max(3, min(args.steps, 10)), stream, flush, torch)
-    q32 = torch.as_tensor(w.q0().astype(np.float32), device="cuda")
-    qo = torch.empty_like(q32)
-    g_ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I_t, w32, q32, qo, stream=stream), 10, stream,
+    qp = torch.as_tensor(pairs_of(w.q0()), device="cuda")
+    qo = torch.empty_like(qp)
+    g_ms = time_op(lambda: rbfsl.rbfsl_gather_dot(I_t, wp, qp, qo, stream=stream, pairs=True), 10, stream,
                    flush, torch)
     ctx.close()
 
@@ -610,12 +627,12 @@ def main():
     pk = peaks()
     w_flops = N * weights_flops(m)
     w_tflops = w_flops / (w_ms * 1e-3) / 1e12
-    g_bytes = N * n * (4 + 4) + N * T * 4 * 2
+    g_bytes = N * n * (8 + 4) + N * T * 8 * 2  # FP32-pair weights and field
     g_gbs = g_bytes / (g_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 solve + f32 trace/gather",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 solves; f32 trace increments and f32-pair gather",
         "data": "synthetic",
         "config": {"workload": "local-deformation N=40962 n=84 ell=4 r^9 T=32 (direct stencils)",
                    "N": N, "n": n, "ell": w.ell, "phs_power": w.power, "tracers": T,
@@ -631,7 +648,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float> (FP64 GEPP, m = 109)",
+        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 GEPP, m = 109)",
                      "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": WEIGHTS_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",
@@ -643,7 +660,9 @@ def main():
                             "frac": wq["f32"]["achieved_gbs"] / pk["hbm_gbs"] if pk.get("hbm_gbs") else None,
                             "traffic": None, "ms_per_launch": wq["f32"]["ms_per_launch"],
                             "fp64": wq["f64"],
-                            "in_step_N40962_T32": {"achieved_gbs": g_gbs, "ms_per_launch": g_ms,
+                            "f32x2": wq["f32x2"],
+                            "in_step_N40962_T32": {"kernel": "gather_dot_pair_kernel<2> (FP32 pairs)",
+                                                   "achieved_gbs": g_gbs, "ms_per_launch": g_ms,
                                                    "note": "W and q fit in L2 at this N"}},
         "cpu_baseline": cpu,
     }

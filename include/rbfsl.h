@@ -70,7 +70,10 @@ enum { RBFSL_PHS = 0, RBFSL_GAUSS = 1, RBFSL_IMQ = 2 };
  * the gather-dot evaluated in FP32 in difference form q_c + sum_j w_j (q_j - q_c). */
 enum { RBFSL_FP64 = 0, RBFSL_MIXED = 1 };
 
-enum { RBFSL_F64 = 0, RBFSL_F32 = 1 };    /* element types of caller buffers */
+/* Element types of caller buffers. RBFSL_F32X2: unevaluated FP32 pairs, value = hi + lo with
+ * |lo| <= ulp(hi)/2, interleaved (hi, lo) per element, 8 bytes each: the storage of weights
+ * and fields in the mixed-precision step (rbfsl_stencil_weights output, rbfsl_gather_dot). */
+enum { RBFSL_F64 = 0, RBFSL_F32 = 1, RBFSL_F32X2 = 2 };
 enum { RBFSL_HOST = 0, RBFSL_DEVICE = 1 }; /* where a caller buffer lives */
 
 /* Limits of this library. */
@@ -116,7 +119,8 @@ int rbfsl_knn_query(const rbfsl_knn_index *index, const double *q, int64_t Nq, i
  * of degree <= ell. Then the interpolant at p_i is sum_j w_ij f_Sj (the system is
  * symmetric). Gaussian elimination with partial pivoting, one warp per point.
  *   x: device N x 3; idx: device Nq x n; p: device Nq x 3; w: device Nq x n of w_dtype
- *   (RBFSL_F64 or RBFSL_F32: FP64 solve, result rounded). status: device Nq or NULL
+ *   (RBFSL_F64, RBFSL_F32 or RBFSL_F32X2: FP64 solve, result rounded or split into an FP32
+ *   pair). status: device Nq or NULL
  *   (RBFSL_ESINGULAR for a zero pivot; w row NaN).
  * Errors: EINVAL (n < 1, ell > RBFSL_MAX_SH_DEGREE, n + (ell+1)^2 > RBFSL_MAX_SYSTEM,
  *   kernel not RBFSL_PHS with odd p >= 1), ECUDA. */
@@ -129,8 +133,12 @@ int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *idx, int64_
  *   q_out[i, t] = q[c, t] + sum_j w[i, j] (q[idx[i,j], t] - q[c, t]),  c = idx[i, 0]
  *                                                          (w_dtype = q_dtype = RBFSL_F32)
  * The difference form equals the first when sum_j w_ij = 1 and keeps FP32 rounding
- * relative to the local variation of q. q_out may not alias q.
- * Errors: EINVAL (mixed dtypes, T < 1, n < 1), ECUDA. */
+ * relative to the local variation of q. dtype RBFSL_F32X2: w, q and q_out are FP32 pairs
+ * (Nq x n x 2, N x T x 2, Nq x T x 2 floats) and the first sum is formed in pair arithmetic
+ * with FP32 operations only (exact high products by FMA, cross terms, two-sum accumulation):
+ * relative rounding ~ n 2^-48 of sum_j |w_ij q_jt| instead of FP32's 2^-24.
+ * q_out may not alias q. A negative idx entry (a failed stencil) gives a NaN row.
+ * Errors: EINVAL (bad dtype, T < 1, n < 1, null pointers, q_out == q), ECUDA. */
 int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q,
                      int T, int dtype, void *q_out, void *stream);
 

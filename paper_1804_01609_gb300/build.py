@@ -65,7 +65,9 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
         flags = common
         if os.path.basename(src) in WHOLE_PROGRAM:
-            flags = [f for f in common if f != "-rdc=true"]
+            # without -rdc the constant-memory tables declared extern in common.cuh become a
+            # (unused) static definition of this unit; nvcc says so in warning 20044
+            flags = [f for f in common if f != "-rdc=true"] + ["-diag-suppress", "20044"]
         cmd = [cc] + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

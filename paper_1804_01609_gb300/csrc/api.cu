@@ -36,6 +36,24 @@ __global__ void convert_kernel(const A *__restrict__ in, B *__restrict__ out, in
     if (i < n) out[i] = (B)in[i];
 }
 
+// Mixed-precision field storage (FP32 pairs, see pair_add) from and to plain arrays.
+template <typename A>
+__global__ void to_pair_kernel(const A *__restrict__ in, float2 *__restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const A v = in[i];
+    const float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (A)hi));
+}
+
+template <typename B>
+__global__ void from_pair_kernel(const float2 *__restrict__ in, B *__restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 v = in[i];
+    out[i] = (B)((double)v.x + (double)v.y);
+}
+
 }  // namespace rbfsl
 
 using namespace rbfsl;
@@ -55,7 +73,7 @@ struct rbfsl_ctx {
     int precision = RBFSL_FP64;
     double dt = 0.0, t = 0.0;
     int T = 0;
-    void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 by precision
+    void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 pairs (mixed), 8 bytes each
     int64_t steps_done = 0;
     // prepared state (local method)
     bool prepared = false;
@@ -66,7 +84,7 @@ struct rbfsl_ctx {
     unsigned long long *ctr = nullptr;  // [singular, knn failures]
     // prepared state (global method)
     double *LU = nullptr, *C64 = nullptr, *Q64 = nullptr;
-    float *C32 = nullptr;
+    float *C32 = nullptr;  // global: FP32 coefficients; RBF-PU: FP32 evaluation (mixed)
     int32_t *perm = nullptr, *piv = nullptr;
     int prepared_T = 0;
     // RBF-PU
@@ -181,12 +199,16 @@ int one_step_global(rbfsl_ctx *c) {
         CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T, RBFSL_F64,
                                      c->q_next, RBFSL_F64, c->stream));
     } else {
-        // FP64 solve of the FP32 field, FP32 evaluation
-        convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q, c->Q64, NT);
+        // FP64 solve of the field (FP32 pairs widened), FP32 evaluation into the freed FP64
+        // right-hand side buffer, stored back as pairs
+        from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, c->Q64, NT);
         CTX_RC(c, global_solve(c->LU, c->perm, N, c->Q64, c->T, c->C64, c->stream));
         convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>(c->C64, c->C32, NT);
+        float *q32 = reinterpret_cast<float *>(c->Q64);
         CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C32, c->T, RBFSL_F32,
-                                     c->q_next, RBFSL_F32, c->stream));
+                                     q32, RBFSL_F32, c->stream));
+        to_pair_kernel<float><<<blocks, 256, 0, c->stream>>>(q32, (float2 *)c->q_next, NT);
+        CTX_RC(c, launch_status("global step (mixed)"));
     }
     std::swap(c->q, c->q_next);
     c->t = t1;
@@ -211,8 +233,10 @@ int prepare_pu(rbfsl_ctx *c) {
     if ((rc = dalloc(c, &c->status, N * sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
     CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
-    if (c->precision == RBFSL_MIXED)
+    if (c->precision == RBFSL_MIXED) {
         if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
+        if ((rc = dalloc(c, &c->C32, N * T * sizeof(float)))) return rc;
+    }
     CTX_RC(c, rbfsl_pu_create(&c->pu, c->X, N, c->pu_centers, c->pu_Mp, R, ell, c->kkind, c->kparam, c->stream));
     c->bytes += c->pu->bytes;
     c->prepared_T = c->T;
@@ -225,12 +249,18 @@ int one_step_pu(rbfsl_ctx *c) {
     const double t1 = c->t + c->dt;
     CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
     const double *q64 = (const double *)c->q;
+    const unsigned blocks = (unsigned)((NT + 255) / 256);
     if (c->precision == RBFSL_MIXED) {
-        convert_kernel<float, double><<<(unsigned)((NT + 255) / 256), 256, 0, c->stream>>>((const float *)c->q, c->Q64, NT);
+        from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, c->Q64, NT);
         q64 = c->Q64;
     }
     CTX_RC(c, rbfsl_pu_apply(c->pu, q64, c->T, c->xi, N, c->pu_wkind,
-                             c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32, c->q_next, c->status, c->stream));
+                             c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32,
+                             c->precision == RBFSL_FP64 ? c->q_next : (void *)c->C32, c->status, c->stream));
+    if (c->precision == RBFSL_MIXED) {
+        to_pair_kernel<float><<<blocks, 256, 0, c->stream>>>(c->C32, (float2 *)c->q_next, NT);
+        CTX_RC(c, launch_status("RBF-PU step (mixed)"));
+    }
     count_status<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->status, N, c->ctr);
     std::swap(c->q, c->q_next);
     c->t = t1;
@@ -258,7 +288,7 @@ int prepare(rbfsl_ctx *c) {
     if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
     if ((rc = dalloc(c, &c->I, N * n * sizeof(int32_t)))) return rc;
     if ((rc = dalloc(c, &c->status, N * sizeof(int32_t)))) return rc;
-    if ((rc = dalloc(c, &c->W, N * n * (c->precision == RBFSL_FP64 ? 8 : 4)))) return rc;
+    if ((rc = dalloc(c, &c->W, N * n * 8))) return rc;  // FP64, or FP32 pairs (mixed)
     if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
     CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
     CTX_RC(c, rbfsl_knn_index_create(&c->knn, c->X, N, (int)n, c->stream));
@@ -305,7 +335,7 @@ int one_step(rbfsl_ctx *c) {
     const int64_t N = c->N;
     const int n = c->n, ell = effective_ell(c), pw = (int)c->kparam;
     const double t1 = c->t + c->dt;
-    const int wdt = c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32;
+    const int wdt = c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2;
     CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
     if (c->mode == RBFSL_DIRECT) {
         CTX_RC(c, launch_knn(c->knn, c->xi, N, n, c->I, c->status, c->stream));
@@ -494,7 +524,6 @@ int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, 
         (mem != RBFSL_HOST && mem != RBFSL_DEVICE))
         return fail(c, RBFSL_EINVAL, "set_tracers: bad arguments");
     DeviceGuard g(c->device);
-    const int es = c->precision == RBFSL_FP64 ? 8 : 4;
     const int64_t cnt = N * (int64_t)T;
     if (T != c->T || !c->q) {
         CTX_TRY(c, cudaStreamSynchronize(c->stream));
@@ -510,17 +539,18 @@ int rbfsl_set_tracers(rbfsl_ctx *c, const void *q, int64_t N, int T, int dtype, 
     }
     const int in_es = dtype == RBFSL_F64 ? 8 : 4;
     const unsigned blocks = (unsigned)((cnt + 255) / 256);
-    if (in_es == es) {
-        CTX_TRY(c, cudaMemcpyAsync(c->q, q, cnt * es,
-                                   mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                                   c->stream));
+    const cudaMemcpyKind kind = mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (c->precision == RBFSL_FP64 && dtype == RBFSL_F64) {
+        CTX_TRY(c, cudaMemcpyAsync(c->q, q, cnt * 8, kind, c->stream));
     } else {
-        // stage the caller's type in q_next, convert into q
-        CTX_TRY(c, cudaMemcpyAsync(c->q_next, q, cnt * in_es,
-                                   mem == RBFSL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                                   c->stream));
-        if (in_es == 8) convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double *)c->q_next, (float *)c->q, cnt);
-        else convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q_next, (double *)c->q, cnt);
+        // stage the caller's type in q_next, convert into q (FP64, or FP32 pairs when mixed)
+        CTX_TRY(c, cudaMemcpyAsync(c->q_next, q, cnt * in_es, kind, c->stream));
+        if (c->precision == RBFSL_FP64)
+            convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q_next, (double *)c->q, cnt);
+        else if (dtype == RBFSL_F64)
+            to_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const double *)c->q_next, (float2 *)c->q, cnt);
+        else
+            to_pair_kernel<float><<<blocks, 256, 0, c->stream>>>((const float *)c->q_next, (float2 *)c->q, cnt);
         CTX_RC(c, launch_status("set_tracers convert"));
     }
     if (mem == RBFSL_HOST) CTX_TRY(c, cudaStreamSynchronize(c->stream));
@@ -545,16 +575,19 @@ int rbfsl_get_q(rbfsl_ctx *c, void *out, int dtype, int mem) {
     if (!out || (dtype != RBFSL_F64 && dtype != RBFSL_F32) || (mem != RBFSL_HOST && mem != RBFSL_DEVICE))
         return fail(c, RBFSL_EINVAL, "get_q: bad arguments");
     DeviceGuard g(c->device);
-    const int es = c->precision == RBFSL_FP64 ? 8 : 4;
     const int out_es = dtype == RBFSL_F64 ? 8 : 4;
     const int64_t cnt = c->N * (int64_t)c->T;
     const cudaMemcpyKind kind = mem == RBFSL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (es == out_es) {
-        CTX_TRY(c, cudaMemcpyAsync(out, c->q, cnt * es, kind, c->stream));
+    if (c->precision == RBFSL_FP64 && dtype == RBFSL_F64) {
+        CTX_TRY(c, cudaMemcpyAsync(out, c->q, cnt * 8, kind, c->stream));
     } else {
         const unsigned blocks = (unsigned)((cnt + 255) / 256);
-        if (es == 8) convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double *)c->q, (float *)c->q_next, cnt);
-        else convert_kernel<float, double><<<blocks, 256, 0, c->stream>>>((const float *)c->q, (double *)c->q_next, cnt);
+        if (c->precision == RBFSL_FP64)
+            convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>((const double *)c->q, (float *)c->q_next, cnt);
+        else if (dtype == RBFSL_F64)
+            from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, (double *)c->q_next, cnt);
+        else
+            from_pair_kernel<float><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, (float *)c->q_next, cnt);
         CTX_RC(c, launch_status("get_q convert"));
         CTX_TRY(c, cudaMemcpyAsync(out, c->q_next, cnt * out_es, kind, c->stream));
     }

@@ -59,12 +59,6 @@ __device__ __forceinline__ Vel<double> dev_vel64(const BatchDesc &p) {
     else u.p1 = 3.14159265358979323846 / p.vel[1];
     return u;
 }
-__device__ __forceinline__ Vel<float> dev_vel32(const BatchDesc &p) {
-    Vel<float> u{p.vel_kind, (float)p.vel[0], (float)p.vel[1], 0.f, 0.f};
-    if (p.vel_kind == RBFSL_VEL_RIGID) { u.p2 = (float)p.vel[2]; u.p3 = (float)p.vel[3]; }
-    else u.p1 = (float)(3.14159265358979323846 / p.vel[1]);
-    return u;
-}
 
 __global__ void batch_trace_kernel(const BatchDesc *__restrict__ d, int np, int64_t total) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -79,8 +73,8 @@ __global__ void batch_trace_kernel(const BatchDesc *__restrict__ d, int np, int6
     if (!b.mixed)
         rk4_point_f64(dev_vel64(b), X[3 * j], X[3 * j + 1], X[3 * j + 2], t1, -b.dt, Xi[3 * j], Xi[3 * j + 1], Xi[3 * j + 2]);
     else
-        rk4_point_mixed(dev_vel32(b), X[3 * j], X[3 * j + 1], X[3 * j + 2], (float)t1, (float)-b.dt,
-                        Xi[3 * j], Xi[3 * j + 1], Xi[3 * j + 2]);
+        rk4_point_mixed(dev_vel64(b), X[3 * j], X[3 * j + 1], X[3 * j + 2], t1, -b.dt, Xi[3 * j], Xi[3 * j + 1],
+                        Xi[3 * j + 2]);
 }
 
 // Shared memory of one point. Direct mode: system region (stencil_doubles), stencil (n int),
@@ -93,7 +87,7 @@ __host__ __device__ inline int batch_point_doubles(int mode, int n, int m, int l
     return batch_region_doubles(mode, n, m, ld) + cap + (cap + 2) / 2;
 }
 
-// Gather-dot of one row from a point's weights (FP64 solution, rounded to FP32 in mixed
+// Gather-dot of one row from a point's weights (FP64 solution, split into FP32 pairs in mixed
 // precision as the single-problem path stores them).
 __device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w, const int32_t *S, int64_t i,
                                              int lane) {
@@ -101,14 +95,14 @@ __device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w
     if (!b.mixed) {
         gather_row<double, double>(w, S, b.n, (const double *)b.q[in], b.T, (double *)b.q[in ^ 1] + i * b.T, lane);
     } else {
-        // round each weight to FP32 first, exactly as a stored FP32 weight row
-        const float *q = (const float *)b.q[in];
-        float *out = (float *)b.q[in ^ 1] + i * b.T;
+        // FP32 pairs: each weight split into a pair exactly as a stored pair weight row, then
+        // the same element arithmetic as gather_dot_pair_kernel
+        const float2 *q = (const float2 *)b.q[in];
+        float2 *out = (float2 *)b.q[in ^ 1] + i * b.T;
         for (int t = lane; t < b.T; t += 32) {
-            const float qc = q[(int64_t)S[0] * b.T + t];
-            float acc = 0.f;
-            for (int j = 0; j < b.n; ++j) acc = fmaf((float)w[j], q[(int64_t)S[j] * b.T + t] - qc, acc);
-            out[t] = qc + acc;
+            float sh = 0.f, sl = 0.f;
+            for (int j = 0; j < b.n; ++j) pair_fma(pair_from(w[j]), q[(int64_t)S[j] * b.T + t], sh, sl);
+            out[t] = pair_norm(sh, sl);
         }
     }
 }
@@ -167,7 +161,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             if (rc != RBFSL_OK) {
                 const int in = (int)(b.step & 1);
                 for (int c = lane; c < b.T; c += 32) {
-                    if (b.mixed) ((float *)b.q[in ^ 1])[i * b.T + c] = NAN;
+                    if (b.mixed) ((float2 *)b.q[in ^ 1])[i * b.T + c] = make_float2(NAN, NAN);
                     else ((double *)b.q[in ^ 1])[i * b.T + c] = NAN;
                 }
             }
@@ -196,7 +190,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
                 } else {
                     const int in = (int)(b.step & 1);
                     for (int c = lane; c < b.T; c += 32) {
-                        if (b.mixed) ((float *)b.q[in ^ 1])[i * b.T + c] = NAN;
+                        if (b.mixed) ((float2 *)b.q[in ^ 1])[i * b.T + c] = make_float2(NAN, NAN);
                         else ((double *)b.q[in ^ 1])[i * b.T + c] = NAN;
                     }
                 }
@@ -434,7 +428,7 @@ int rbfsl_batch_add(rbfsl_batch *b, const rbfsl_problem *pr, int *id_out) {
         h.bytes += bytes;
         return RBFSL_OK;
     };
-    const size_t es = pr->precision == RBFSL_FP64 ? 8 : 4;
+    const size_t es = 8;  // FP64, or an FP32 pair (mixed)
     if ((rc = alloc((void **)&h.X, N * 3 * sizeof(double))) || (rc = alloc((void **)&h.xi, N * 3 * sizeof(double))) ||
         (rc = alloc((void **)&h.status, N * sizeof(int32_t))) || (rc = alloc(&h.q[0], N * pr->T * es)) ||
         (rc = alloc(&h.q[1], N * pr->T * es)) || (rc = alloc((void **)&h.ctr, 2 * sizeof(unsigned long long)))) {
@@ -447,8 +441,12 @@ int rbfsl_batch_add(rbfsl_batch *b, const rbfsl_problem *pr, int *id_out) {
     if (pr->precision == RBFSL_FP64) {
         RBFSL_CUDA_TRY(cudaMemcpyAsync(h.q[0], pr->q0, N * pr->T * 8, cudaMemcpyHostToDevice, s));
     } else {
-        std::vector<float> q32((size_t)N * pr->T);
-        for (size_t e = 0; e < q32.size(); ++e) q32[e] = (float)pr->q0[e];
+        std::vector<float> q32((size_t)N * pr->T * 2);
+        for (size_t e = 0; e < (size_t)N * pr->T; ++e) {
+            const float hi = (float)pr->q0[e];
+            q32[2 * e] = hi;
+            q32[2 * e + 1] = (float)(pr->q0[e] - (double)hi);
+        }
         RBFSL_CUDA_TRY(cudaMemcpyAsync(h.q[0], q32.data(), q32.size() * 4, cudaMemcpyHostToDevice, s));
         RBFSL_CUDA_TRY(cudaStreamSynchronize(s));
     }
@@ -565,10 +563,10 @@ int rbfsl_batch_get_q(rbfsl_batch *b, int id, double *out) {
         RBFSL_CUDA_TRY(cudaMemcpyAsync(out, src, cnt * 8, cudaMemcpyDeviceToHost, b->stream));
         RBFSL_CUDA_TRY(cudaStreamSynchronize(b->stream));
     } else {
-        std::vector<float> tmp(cnt);
-        RBFSL_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, cnt * 4, cudaMemcpyDeviceToHost, b->stream));
+        std::vector<float> tmp(cnt * 2);
+        RBFSL_CUDA_TRY(cudaMemcpyAsync(tmp.data(), src, cnt * 8, cudaMemcpyDeviceToHost, b->stream));
         RBFSL_CUDA_TRY(cudaStreamSynchronize(b->stream));
-        for (size_t e = 0; e < cnt; ++e) out[e] = tmp[e];
+        for (size_t e = 0; e < cnt; ++e) out[e] = (double)tmp[2 * e] + (double)tmp[2 * e + 1];
     }
     return RBFSL_OK;
 }

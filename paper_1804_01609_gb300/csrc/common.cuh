@@ -111,4 +111,45 @@ __device__ __forceinline__ double sqdist_rn(double ax, double ay, double az, dou
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// ---------------------------------------------------------------------------------------
+// Mixed-precision storage of fields and weights: each value is an unevaluated pair of FP32
+// numbers (hi, lo), value = hi + lo with |lo| <= ulp(hi) / 2, stored interleaved (8 bytes per
+// value). The gather-dot sum is formed in pair arithmetic with FP32 operations only: exact
+// products of the high parts (FMA error term), the cross terms, and Knuth's two-sum into the
+// accumulator, so a step adds ~n 2^-48 relative rounding instead of the ~2^-24 of plain FP32.
+
+__device__ __forceinline__ float2 pair_from(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+// (sh, sl) += w * q for pairs w and q; w.lo * q.lo (below 2^-48 |w q|) is dropped.
+__device__ __forceinline__ void pair_fma(float2 w, float2 q, float &sh, float &sl) {
+    const float p = w.x * q.x;
+    float pe = fmaf(w.x, q.x, -p);
+    pe = fmaf(w.x, q.y, pe);
+    pe = fmaf(w.y, q.x, pe);
+    const float s = sh + p;
+    const float bp = s - sh;
+    const float e = (sh - (s - bp)) + (p - bp);
+    sl = sl + (e + pe);
+    sh = s;
+}
+
+// The accumulator as a normalised pair (fast two-sum).
+__device__ __forceinline__ float2 pair_norm(float sh, float sl) {
+    const float hi = sh + sl;
+    return make_float2(hi, sl - (hi - sh));
+}
+
+// Weight and field element conversions from FP64 results.
+template <typename WT>
+__device__ __forceinline__ WT wcast(double v);
+template <>
+__device__ __forceinline__ double wcast<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float wcast<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ float2 wcast<float2>(double v) { return pair_from(v); }
+
 }  // namespace rbfsl

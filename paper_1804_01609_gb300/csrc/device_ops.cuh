@@ -58,27 +58,84 @@ __device__ __forceinline__ void rk4_point_f64(const Vel<double> &u, double x, do
     normalize3(ox, oy, oz);
 }
 
-// Mixed: stages in FP32; the displacement d = (h/6)(k1 + 2k2 + 2k3 + k4) is added to the FP64
-// node and projected in FP64, so the FP32 rounding scales with |d|, not with |x|.
-__device__ __forceinline__ void rk4_point_mixed(const Vel<float> &u, double xd, double yd, double zd,
-                                                float t1, float h, double &ox, double &oy,
+// Mixed: increment form. The node's own velocity U0 = u(x, t1), the stage displacements' FP64
+// parts and the final add and projection are FP64 (a few dozen flops per node); the RK4 stages
+// are FP32 increments from the node. A stage point is x + e with e = N(x + a) - x formed in
+// FP32 from the stage displacement a (|a| ~ |u| dt), and its velocity is U0 + D with
+// D = u(x + e, t_s) - u(x, t1) formed in FP32 from e and the FP64 difference of the time
+// factors, so every FP32 rounding error scales with an increment, not with |x| or |u|.
+// Unit nodes are assumed (|x| = 1 to FP64 rounding).
+
+// e = N(x + a) - x for unit x: r = |x + a| = sqrt(1 + 2 x.a + a.a),
+// e = (a - x (r - 1)) / r with r - 1 = (2 x.a + a.a) / (r + 1).
+__device__ __forceinline__ void stage_offset(float x, float y, float z, float ax, float ay, float az,
+                                             float &ex, float &ey, float &ez) {
+    const float g = 2.0f * (x * ax + y * ay + z * az) + (ax * ax + ay * ay + az * az);
+    const float r = sqrtf(1.0f + g);
+    const float rm1 = g / (r + 1.0f);
+    const float ir = 1.0f / r;
+    ex = (ax - x * rm1) * ir;
+    ey = (ay - y * rm1) * ir;
+    ez = (az - z * rm1) * ir;
+}
+
+// D = u(x + e, t_s) - u(x, t1). Rigid rotation: omega x e. Deformation u = c(t) g(x) with
+// g = 2 kappa y (-z, 0, x): D = c_s [g(x + e) - g(x)] + (c_s - c_1) g(x), the bracket expanded
+// so that it is formed from products with e only.
+__device__ __forceinline__ void vel_increment(int kind, float w0, float w1, float w2, float k2,
+                                              float cs, float dc, float x, float y, float z,
+                                              float ex, float ey, float ez, float &dx, float &dy,
+                                              float &dz) {
+    if (kind == RBFSL_VEL_RIGID) {
+        dx = w1 * ez - w2 * ey;
+        dy = w2 * ex - w0 * ez;
+        dz = w0 * ey - w1 * ex;
+    } else {
+        const float gx = -k2 * ((y * ez + ey * z) + ey * ez);  // g(x + e) - g(x), x-component
+        const float gz = k2 * ((y * ex + ey * x) + ey * ex);
+        const float bx = -k2 * y * z, bz = k2 * y * x;         // g(x)
+        dx = cs * gx + dc * bx;
+        dy = 0.0f;
+        dz = cs * gz + dc * bz;
+    }
+}
+
+__device__ __forceinline__ void rk4_point_mixed(const Vel<double> &u, double xd, double yd, double zd,
+                                                double t1, double h, double &ox, double &oy,
                                                 double &oz) {
+    double U0x, U0y, U0z;
+    u(xd, yd, zd, t1, U0x, U0y, U0z);
+    // time factors of the deformation at t1, t1 + h/2, t1 + h (FP64); unused for rigid rotation
+    float cs2 = 0.f, dc2 = 0.f, cs4 = 0.f, dc4 = 0.f, k2 = 0.f, w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    if (u.kind == RBFSL_VEL_RIGID) {
+        w0 = (float)(u.p3 * u.p0); w1 = (float)(u.p3 * u.p1); w2 = (float)(u.p3 * u.p2);
+    } else {
+        const double c1 = cos(u.p1 * t1), c2 = cos(u.p1 * (t1 + 0.5 * h)), c4 = cos(u.p1 * (t1 + h));
+        cs2 = (float)c2; dc2 = (float)(c2 - c1);
+        cs4 = (float)c4; dc4 = (float)(c4 - c1);
+        k2 = (float)(2.0 * u.p0);
+    }
     const float x = (float)xd, y = (float)yd, z = (float)zd;
-    float k1x, k1y, k1z, k2x, k2y, k2z, k3x, k3y, k3z, k4x, k4y, k4z;
-    u(x, y, z, t1, k1x, k1y, k1z);
-    float sx = x + 0.5f * h * k1x, sy = y + 0.5f * h * k1y, sz = z + 0.5f * h * k1z;
-    normalize3(sx, sy, sz);
-    u(sx, sy, sz, t1 + 0.5f * h, k2x, k2y, k2z);
-    sx = x + 0.5f * h * k2x; sy = y + 0.5f * h * k2y; sz = z + 0.5f * h * k2z;
-    normalize3(sx, sy, sz);
-    u(sx, sy, sz, t1 + 0.5f * h, k3x, k3y, k3z);
-    sx = x + h * k3x; sy = y + h * k3y; sz = z + h * k3z;
-    normalize3(sx, sy, sz);
-    u(sx, sy, sz, t1 + h, k4x, k4y, k4z);
-    const float c = h / 6.0f;
-    ox = xd + (double)(c * (k1x + 2.0f * k2x + 2.0f * k3x + k4x));
-    oy = yd + (double)(c * (k1y + 2.0f * k2y + 2.0f * k3y + k4y));
-    oz = zd + (double)(c * (k1z + 2.0f * k2z + 2.0f * k3z + k4z));
+    const float hf = (float)h, hh = (float)(0.5 * h);
+    // stage 2: a2 = (h/2) U0
+    const float a2x = (float)(0.5 * h * U0x), a2y = (float)(0.5 * h * U0y), a2z = (float)(0.5 * h * U0z);
+    float ex, ey, ez, d2x, d2y, d2z, d3x, d3y, d3z, d4x, d4y, d4z;
+    stage_offset(x, y, z, a2x, a2y, a2z, ex, ey, ez);
+    vel_increment(u.kind, w0, w1, w2, k2, cs2, dc2, x, y, z, ex, ey, ez, d2x, d2y, d2z);
+    // stage 3: a3 = (h/2)(U0 + D2)
+    stage_offset(x, y, z, a2x + hh * d2x, a2y + hh * d2y, a2z + hh * d2z, ex, ey, ez);
+    vel_increment(u.kind, w0, w1, w2, k2, cs2, dc2, x, y, z, ex, ey, ez, d3x, d3y, d3z);
+    // stage 4: a4 = h (U0 + D3)
+    const float a4x = (float)(h * U0x), a4y = (float)(h * U0y), a4z = (float)(h * U0z);
+    stage_offset(x, y, z, a4x + hf * d3x, a4y + hf * d3y, a4z + hf * d3z, ex, ey, ez);
+    vel_increment(u.kind, w0, w1, w2, k2, cs4, dc4, x, y, z, ex, ey, ez, d4x, d4y, d4z);
+    // d = (h/6)(k1 + 2 k2 + 2 k3 + k4) = h U0 + (h/6)(2 D2 + 2 D3 + D4)
+    const float c6 = (float)(h / 6.0);
+    const float ix = c6 * (2.0f * (d2x + d3x) + d4x), iy = c6 * (2.0f * (d2y + d3y) + d4y),
+                iz = c6 * (2.0f * (d2z + d3z) + d4z);
+    ox = xd + (h * U0x + (double)ix);
+    oy = yd + (h * U0y + (double)iy);
+    oz = zd + (h * U0z + (double)iz);
     normalize3(ox, oy, oz);
 }
 
@@ -88,13 +145,6 @@ inline Vel<double> make_vel64(int kind, const double *prm) {
     Vel<double> u{kind, prm[0], prm[1], 0.0, 0.0};
     if (kind == RBFSL_VEL_RIGID) { u.p2 = prm[2]; u.p3 = prm[3]; }
     else u.p1 = pi / prm[1];
-    return u;
-}
-inline Vel<float> make_vel32(int kind, const double *prm) {
-    const double pi = 3.14159265358979323846;
-    Vel<float> u{kind, (float)prm[0], (float)prm[1], 0.f, 0.f};
-    if (kind == RBFSL_VEL_RIGID) { u.p2 = (float)prm[2]; u.p3 = (float)prm[3]; }
-    else u.p1 = (float)(pi / prm[1]);
     return u;
 }
 

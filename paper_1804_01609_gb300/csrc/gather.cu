@@ -5,7 +5,10 @@
 //
 // A row group of L lanes (L = the power of two >= min(T, 32)) serves one output row; the
 // group's first n (w, idx) pairs are loaded cooperatively, one per lane, and broadcast with
-// warp shuffles. FP32 uses the difference form q_c + sum_j w_j (q_j - q_c), c = idx[i, 0].
+// warp shuffles. FP32 uses the difference form q_c + sum_j w_j (q_j - q_c), c = idx[i, 0];
+// FP32 pairs (the mixed-precision storage) use pair arithmetic.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -112,9 +115,81 @@ __global__ void __launch_bounds__(256) gather_dot_vec_kernel(const int32_t *__re
     }
 }
 
+// FP32 pairs (mixed precision): weights and field stored as (hi, lo) pairs and the sum
+// formed in pair arithmetic (pair_fma), FP32 operations only. Each lane owns V consecutive
+// tracers (V = 2: one 16-byte load per gathered row piece; V = 1 for odd T); a row group of G
+// lanes covers G * V tracers per pass. Same element order (j ascending) as the batched path.
+template <int V>
+__global__ void __launch_bounds__(256) gather_dot_pair_kernel(const int32_t *__restrict__ idx,
+                                                              const float2 *__restrict__ W, int64_t Nq,
+                                                              int n, const float2 *__restrict__ q,
+                                                              int T, int G, float2 *__restrict__ out) {
+    using Vec = typename std::conditional<V == 2, float4, float2>::type;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rows_per_warp = kWarp / G;
+    const int sub = lane % G, grp = lane / G;
+    const int64_t i = gwarp * rows_per_warp + grp;
+    const bool active = i < Nq;
+    if (__all_sync(0xffffffffu, !active)) return;
+    for (int t0 = 0; t0 < T; t0 += G * V) {
+        const int t = t0 + sub * V;
+        const bool tv = active && t < T;  // V = 2 only for even T, so t + 1 < T too
+        float sh[V], sl[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) { sh[v] = 0.f; sl[v] = 0.f; }
+        for (int j0 = 0; j0 < n; j0 += G) {
+            float2 wj = make_float2(0.f, 0.f);
+            int sj = 0;
+            if (active && j0 + sub < n) {
+                wj = W[i * n + j0 + sub];
+                sj = idx[i * n + j0 + sub];
+            }
+            const int cnt = min(G, n - j0);
+            for (int jj = 0; jj < cnt; ++jj) {
+                const int src = grp * G + jj;
+                const float2 w = make_float2(__shfl_sync(0xffffffffu, wj.x, src), __shfl_sync(0xffffffffu, wj.y, src));
+                const int sidx = __shfl_sync(0xffffffffu, sj, src);
+                if (tv) {
+                    const Vec x = sidx >= 0 ? *reinterpret_cast<const Vec *>(q + (int64_t)sidx * T + t) : Vec{};
+                    const float2 *xp = reinterpret_cast<const float2 *>(&x);
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        pair_fma(w, sidx >= 0 ? xp[v] : make_float2(NAN, NAN), sh[v], sl[v]);
+                }
+            }
+        }
+        if (tv) {
+            Vec o;
+            float2 *op = reinterpret_cast<float2 *>(&o);
+#pragma unroll
+            for (int v = 0; v < V; ++v) op[v] = pair_norm(sh[v], sl[v]);
+            *reinterpret_cast<Vec *>(out + i * T + t) = o;
+        }
+    }
+}
+
 int launch_gather(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q, int T,
                   int dtype, void *q_out, cudaStream_t s) {
     if (Nq == 0) return RBFSL_OK;
+    if (dtype == RBFSL_F32X2) {
+        const bool vec2 = T % 2 == 0 && ((uintptr_t)q % 16 == 0) && ((uintptr_t)q_out % 16 == 0);
+        const int per_lane = vec2 ? 2 : 1;
+        const int need = (T + per_lane - 1) / per_lane;
+        int G = 1;
+        while (G < need && G < 32) G <<= 1;
+        const int rows_per_warp = kWarp / G;
+        const int threads = 256;
+        const int64_t warps = (Nq + rows_per_warp - 1) / rows_per_warp;
+        const unsigned blocks = (unsigned)((warps * kWarp + threads - 1) / threads);
+        if (vec2)
+            gather_dot_pair_kernel<2><<<blocks, threads, 0, s>>>(idx, (const float2 *)w, Nq, n, (const float2 *)q, T,
+                                                                  G, (float2 *)q_out);
+        else
+            gather_dot_pair_kernel<1><<<blocks, threads, 0, s>>>(idx, (const float2 *)w, Nq, n, (const float2 *)q, T,
+                                                                  G, (float2 *)q_out);
+        return launch_status("gather_dot_pair");
+    }
     const int V = dtype == RBFSL_F64 ? 2 : 4;
     const bool aligned = ((uintptr_t)q % 16 == 0) && ((uintptr_t)q_out % 16 == 0);
     if (T % V == 0 && T / V <= 32 && aligned) {
@@ -155,7 +230,7 @@ extern "C" int rbfsl_gather_dot(const int32_t *idx, const void *w, int64_t Nq, i
                                 const void *q, int T, int dtype, void *q_out, void *stream) {
     using namespace rbfsl;
     RBFSL_CHECK_ARG(Nq >= 0 && n >= 1 && T >= 1, "gather_dot: bad sizes");
-    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32, "gather_dot: bad dtype");
+    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32 || dtype == RBFSL_F32X2, "gather_dot: bad dtype");
     RBFSL_CHECK_ARG(Nq == 0 || (idx && w && q && q_out), "gather_dot: null pointer");
     RBFSL_CHECK_ARG(q != q_out, "gather_dot: q_out aliases q");
     return launch_gather(idx, w, Nq, n, q, T, dtype, q_out, (cudaStream_t)stream);

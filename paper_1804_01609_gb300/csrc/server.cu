@@ -54,7 +54,7 @@ struct Req {
 // grid index, stencil factors or patch factors).
 size_t estimate_bytes(const rbfsl_request &r) {
     const double N = (double)r.problem.N, T = r.problem.T;
-    const double es = r.problem.precision == RBFSL_FP64 ? 8.0 : 4.0;
+    const double es = 8.0;  // FP64 or FP32-pair weights
     const int M = (r.problem.ell + 1) * (r.problem.ell + 1);
     double b = N * (24 + 24 + 4) + 2.0 * N * T * 8.0 + N * 28.0 + 64.0 * 1024 * 1024;
     if (r.method == RBFSL_LOCAL) {

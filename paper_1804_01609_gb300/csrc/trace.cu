@@ -1,7 +1,7 @@
 // Departure-point tracing (Sec. 3.2, Eq. sl_ode): RK4 backward in time with an orthogonal
 // projection onto S^2 at every stage and of the result. One thread per node: the work per
 // node is ~200 flops with no reuse, so the kernel is bound by the FP64 pipe (FP64 mode) or
-// by the 24+24 bytes per node it moves (mixed mode).
+// by the 24+24 bytes per node it moves (mixed mode, where ~50 of the flops are FP64).
 #include "common.cuh"
 #include "kernels.cuh"
 #include "device_ops.cuh"
@@ -16,9 +16,9 @@ __global__ void trace_rk4_f64(const double *__restrict__ X, int64_t N, Vel<doubl
     rk4_point_f64(u, X[3 * j], X[3 * j + 1], X[3 * j + 2], t1, h, Xi[3 * j], Xi[3 * j + 1], Xi[3 * j + 2]);
 }
 
-// Mixed tracer: FP32 stages, FP64 displacement add and projection.
-__global__ void trace_rk4_mixed(const double *__restrict__ X, int64_t N, Vel<float> u, float t1,
-                                float h, double *__restrict__ Xi) {
+// Mixed tracer: FP32 stage increments, FP64 node velocity, final add and projection.
+__global__ void trace_rk4_mixed(const double *__restrict__ X, int64_t N, Vel<double> u, double t1,
+                                double h, double *__restrict__ Xi) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= N) return;
     rk4_point_mixed(u, X[3 * j], X[3 * j + 1], X[3 * j + 2], t1, h, Xi[3 * j], Xi[3 * j + 1], Xi[3 * j + 2]);
@@ -32,10 +32,7 @@ int launch_trace(const double *x, int64_t N, int vel_kind, const double *prm, do
     if (precision == RBFSL_FP64) {
         trace_rk4_f64<<<blocks, threads, 0, s>>>(x, N, make_vel64(vel_kind, prm), t1, -dt, xi);
     } else {
-        const Vel<float> u = make_vel32(vel_kind, prm);
-        // The deformation's time argument enters through cos(pi t / T_f); FP32 t1 is exact
-        // to ~1e-7 relative, far below the trajectory error of a step.
-        trace_rk4_mixed<<<blocks, threads, 0, s>>>(x, N, u, (float)t1, (float)-dt, xi);
+        trace_rk4_mixed<<<blocks, threads, 0, s>>>(x, N, make_vel64(vel_kind, prm), t1, -dt, xi);
     }
     return launch_status("trace_rk4");
 }

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(NW == 8 ? 256 : 128) weights_kernel(WeightsArg
                                      a.P[3 * i], a.P[3 * i + 1], a.P[3 * i + 2], t);
     if (t >= kWarp) return;
     const int n = a.n, lane = t;
-    for (int j = lane; j < n; j += kWarp) W[i * n + j] = rc == RBFSL_OK ? (WT)A[j * a.ld + a.m] : (WT)NAN;
+    for (int j = lane; j < n; j += kWarp) W[i * n + j] = wcast<WT>(rc == RBFSL_OK ? A[j * a.ld + a.m] : (double)NAN);
     if (a.status && lane == 0) a.status[i] = rc;
 }
 
@@ -89,6 +89,13 @@ int launch_weights_nw(const WeightsArgs &a, int spb, void *w, cudaStream_t s) {
     const unsigned blocks = (unsigned)((a.Nq + spb - 1) / spb);
     weights_kernel<NW, WT><<<blocks, spb * NW * kWarp, smem, s>>>(a, (WT *)w);
     return launch_status("stencil_weights");
+}
+
+template <int NW>
+int launch_weights_typed(const WeightsArgs &a, int spb, void *w, int w_dtype, cudaStream_t s) {
+    if (w_dtype == RBFSL_F64) return launch_weights_nw<NW, double>(a, spb, w, s);
+    if (w_dtype == RBFSL_F32X2) return launch_weights_nw<NW, float2>(a, spb, w, s);
+    return launch_weights_nw<NW, float>(a, spb, w, s);
 }
 
 int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int ell, int power,
@@ -111,15 +118,10 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
             const char *e = getenv("RBFSL_WEIGHTS_WARPS");
             return (e && atoi(e) == 8) ? 8 : 4;
         }();
-        if (nw == 8)
-            return w_dtype == RBFSL_F64 ? launch_weights_nw<8, double>(a, 1, w, s)
-                                        : launch_weights_nw<8, float>(a, 1, w, s);
-        return w_dtype == RBFSL_F64 ? launch_weights_nw<4, double>(a, 1, w, s)
-                                    : launch_weights_nw<4, float>(a, 1, w, s);
+        if (nw == 8) return launch_weights_typed<8>(a, 1, w, w_dtype, s);
+        return launch_weights_typed<4>(a, 1, w, w_dtype, s);
     }
-    const int spb = 4;  // four independent points (warps) per block
-    return w_dtype == RBFSL_F64 ? launch_weights_nw<1, double>(a, spb, w, s)
-                                : launch_weights_nw<1, float>(a, spb, w, s);
+    return launch_weights_typed<1>(a, 4, w, w_dtype, s);  // four independent points (warps) per block
 }
 
 // Centre-stencil weights, one warp per point (see center_point): bound by HBM bandwidth
@@ -138,14 +140,14 @@ __global__ void __launch_bounds__(128) center_weights_kernel(
     double *b = sm + (size_t)warp * 2 * m, *y = b + m;
     const int64_t k = Kc[i];
     if (k < 0) {
-        for (int j = lane; j < n; j += 32) { W[i * n + j] = (WT)NAN; I[i * n + j] = -1; }
+        for (int j = lane; j < n; j += 32) { W[i * n + j] = wcast<WT>((double)NAN); I[i * n + j] = -1; }
         if (status && lane == 0) status[i] = RBFSL_EKNN;
         return;
     }
     for (int j = lane; j < n; j += 32) I[i * n + j] = Ik[k * n + j];
     center_point(X, Ik + k * n, LU + (size_t)k * m * m, perm + (size_t)k * m, n, m, ell, half,
                  P[3 * i], P[3 * i + 1], P[3 * i + 2], b, y, lane);
-    for (int j = lane; j < n; j += 32) W[i * n + j] = (WT)y[j];
+    for (int j = lane; j < n; j += 32) W[i * n + j] = wcast<WT>(y[j]);
     if (status && lane == 0) status[i] = RBFSL_OK;
 }
 
@@ -162,6 +164,9 @@ int launch_center_weights(const double *X, const int32_t *K, const int32_t *Ik, 
     if (w_dtype == RBFSL_F64)
         center_weights_kernel<double><<<blocks, 128, smem, s>>>(X, K, Ik, LU, perm, Nq, n, ell, (power - 1) / 2,
                                                                 p, I, (double *)w, status);
+    else if (w_dtype == RBFSL_F32X2)
+        center_weights_kernel<float2><<<blocks, 128, smem, s>>>(X, K, Ik, LU, perm, Nq, n, ell, (power - 1) / 2,
+                                                                p, I, (float2 *)w, status);
     else
         center_weights_kernel<float><<<blocks, 128, smem, s>>>(X, K, Ik, LU, perm, Nq, n, ell, (power - 1) / 2,
                                                                p, I, (float *)w, status);
@@ -182,7 +187,8 @@ extern "C" int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *
     const int pw = (int)kparam;
     RBFSL_CHECK_ARG(kernel == RBFSL_PHS && (double)pw == kparam && pw >= 1 && (pw & 1),
                     "stencil_weights: only the PHS kernel r^p with odd p is supported");
-    RBFSL_CHECK_ARG(w_dtype == RBFSL_F64 || w_dtype == RBFSL_F32, "stencil_weights: bad w_dtype");
+    RBFSL_CHECK_ARG(w_dtype == RBFSL_F64 || w_dtype == RBFSL_F32 || w_dtype == RBFSL_F32X2,
+                    "stencil_weights: bad w_dtype");
     RBFSL_CHECK_ARG(Nq == 0 || (x && idx && p && w), "stencil_weights: null pointer");
     return launch_weights(x, idx, Nq, n, ell, pw, p, w, w_dtype, status, (cudaStream_t)stream);
 }

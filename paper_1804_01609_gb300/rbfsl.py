@@ -21,7 +21,7 @@ LOCAL, GLOBAL, PU = 0, 1, 2
 DIRECT, CENTER = 0, 1
 PHS, GAUSS, IMQ = 0, 1, 2
 FP64, MIXED = 0, 1
-F64, F32 = 0, 1
+F64, F32, F32X2 = 0, 1, 2
 HOST, DEVICE = 0, 1
 PU_WENDLAND, PU_BSPLINE = 0, 1
 
@@ -199,16 +199,30 @@ def rbfsl_knn_query(index, q, k, idx, status=None, stream=None):
                                   _ptr(status), _stream(stream)))
 
 
+def _weights_code(w):
+    """float64 / float32 N x n, or N x n x 2 float32 (FP32 pairs, RBFSL_F32X2)."""
+    import torch
+    if w.dim() == 3 and w.shape[2] == 2 and w.dtype == torch.float32:
+        return F32X2
+    return _dtype_code(w)
+
+
 def rbfsl_stencil_weights(x, idx, n, ell, kernel, kparam, p, w, status=None, stream=None):
     _check(load().rbfsl_stencil_weights(_ptr(x), x.shape[0], _ptr(idx), p.shape[0], n, ell,
-                                        kernel, float(kparam), _ptr(p), _ptr(w), _dtype_code(w),
+                                        kernel, float(kparam), _ptr(p), _ptr(w), _weights_code(w),
                                         _ptr(status), _stream(stream)))
 
 
-def rbfsl_gather_dot(idx, w, q, q_out, stream=None):
-    T = q.shape[1] if q.dim() == 2 else 1
+def rbfsl_gather_dot(idx, w, q, q_out, stream=None, pairs=False):
+    """pairs=True: w, q and q_out are FP32 pairs (Nq x n x 2, N x T x 2, Nq x T x 2 float32)."""
+    if pairs:
+        if q.dim() != 3 or q.shape[2] != 2 or _weights_code(w) != F32X2:
+            raise ValueError("pairs=True wants q of shape N x T x 2 and w of shape Nq x n x 2 (float32)")
+        T, code = q.shape[1], F32X2
+    else:
+        T, code = (q.shape[1] if q.dim() == 2 else 1), _dtype_code(q)
     _check(load().rbfsl_gather_dot(_ptr(idx), _ptr(w), idx.shape[0], idx.shape[1], _ptr(q), T,
-                                   _dtype_code(q), _ptr(q_out), _stream(stream)))
+                                   code, _ptr(q_out), _stream(stream)))
 
 
 def rbfsl_global_factor(x, kernel, eps, LU, perm, stream=None):
@@ -537,14 +551,15 @@ class Context:
         return xi.value, idx.value, w.value
 
     def last_step_tensors(self, n, weights_dtype):
-        """Copies of the last step's departure points (N x 3), stencils (N x n) and
-        weights (N x n, weights_dtype) as torch tensors."""
+        """Copies of the last step's departure points (N x 3), stencils (N x n) and weights as
+        torch tensors: N x n float64 (weights_dtype float64, the FP64 step) or N x n x 2 float32
+        FP32 pairs (weights_dtype float32, the mixed-precision step)."""
         import torch
         xi, idx, w = self.last_step_buffers()
         torch.cuda.synchronize()
-        wt = "<f8" if weights_dtype == torch.float64 else "<f4"
+        wt, wshape = ("<f8", (self.N, n)) if weights_dtype == torch.float64 else ("<f4", (self.N, n, 2))
         out = []
-        for ptr, shape, ts in ((xi, (self.N, 3), "<f8"), (idx, (self.N, n), "<i4"), (w, (self.N, n), wt)):
+        for ptr, shape, ts in ((xi, (self.N, 3), "<f8"), (idx, (self.N, n), "<i4"), (w, wshape, wt)):
             out.append(None if not ptr else torch.as_tensor(_DeviceView(ptr, shape, ts), device="cuda").clone())
         return tuple(out)
 

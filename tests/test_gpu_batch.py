@@ -51,8 +51,7 @@ def _ctx(P, steps):
     c.set_kernel(rbfsl.PHS, P["power"])
     c.set_precision(P["precision"])
     c.set_dt(P["dt"])
-    q = P["q0"].astype(np.float32) if P["precision"] == rbfsl.MIXED else P["q0"]
-    c.set_tracers(q)
+    c.set_tracers(P["q0"])  # FP64 in both precisions: mixed stores it as FP32 pairs, like the batch
     c.step(steps)
     out = c.get_q()
     c.close()

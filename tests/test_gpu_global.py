@@ -103,7 +103,7 @@ def _ctx(w, precision, steps):
     ctx.set_kernel(rbfsl.GAUSS, w.eps)
     ctx.set_precision(precision)
     ctx.set_dt(w.dt)
-    ctx.set_tracers(w.q0() if precision == rbfsl.FP64 else w.q0().astype(np.float32))
+    ctx.set_tracers(w.q0())
     ctx.step(steps)
     q = ctx.get_q()
     ctx.close()

@@ -2,7 +2,8 @@
 
 Tolerances (FP64 unless stated):
   departure points        1e-14 absolute (RK4 with the same stage order; rounding only)
-  mixed departure points  5e-8 absolute (FP32 stages, displacement ~ omega dt)
+  mixed departure points  1e-10 absolute (increment form: FP32 rounding scales with the stage
+                          increments ~ |grad u| |u| dt^2, the node's own velocity is FP64)
   k-NN                    bit-exact indices vs brute force on the same points
   weights, n=31 ell=2     1e-10 relative to max|w| (the workload's stated bound; FP64 weights are
                           determined to ~3e-13 at this size)
@@ -56,7 +57,7 @@ def test_trace_parity(orc, kind):
     assert np.abs(xi.cpu().numpy() - ref).max() < 1e-14
     rbfsl.rbfsl_trace_rk4(x, kind, prm, t1, dt, rbfsl.MIXED, xi)
     got = xi.cpu().numpy()
-    assert np.abs(got - ref).max() < 5e-8
+    assert np.abs(got - ref).max() < 1e-10
     np.testing.assert_allclose(np.linalg.norm(got, axis=1), 1.0, atol=1e-15)
 
 
@@ -179,6 +180,46 @@ def test_gather_dot_parity(T):
     rbfsl.rbfsl_gather_dot(_t(I, torch.int32), _t(W, torch.float32), _t(q, torch.float32), out32)
     err = np.abs(out32.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err < 1e-5
+
+
+def _to_pairs(q):
+    hi = q.astype(np.float32)
+    return np.stack([hi, (q - hi.astype(np.float64)).astype(np.float32)], axis=-1)
+
+
+@pytest.mark.parametrize("T", [1, 5, 33, 64])
+def test_gather_dot_pairs(T):
+    """FP32 pairs (the mixed-precision storage of w and q): the result equals the exact
+    sum_j w_j q_j of the pairs' values within the pair arithmetic's rounding,
+    2 (n + 8) 2^-48 sum_j |w_j| |q_j|, plus the output pair's own 2^-46 |result|; pairs come back
+    normalised; small-integer data, whose sums are exact in FP32, come back bit for bit."""
+    N, n = 20000, 55
+    rng = np.random.default_rng(100 + T)
+    I = rng.integers(0, N, (N, n)).astype(np.int32)
+    W = rng.standard_normal((N, n))
+    W /= W.sum(1, keepdims=True)
+    q = rng.standard_normal((N, T)) + 3.0
+    Wp, qp = _to_pairs(W), _to_pairs(q)
+    wv = Wp[..., 0].astype(np.float64) + Wp[..., 1].astype(np.float64)
+    qv = qp[..., 0].astype(np.float64) + qp[..., 1].astype(np.float64)
+    out = torch.empty((N, T, 2), dtype=torch.float32, device=DEV)
+    rbfsl.rbfsl_gather_dot(_t(I, torch.int32), _t(Wp, torch.float32), _t(qp, torch.float32), out, pairs=True)
+    got = out.cpu().numpy()
+    gv = got[..., 0].astype(np.float64) + got[..., 1].astype(np.float64)
+    ref = np.einsum("ij,ijt->it", wv, qv[I])
+    bound = 2 * (n + 8) * 2.0 ** -48 * np.einsum("ij,ijt->it", np.abs(wv), np.abs(qv[I])) + 2.0 ** -46 * np.abs(ref)
+    assert np.all(np.abs(gv - ref) <= bound)
+    # the pair storage is ~2^24 times more accurate than FP32: the error is far below FP32 rounding
+    assert np.abs(gv - ref).max() < 1e-3 * 2.0 ** -24 * np.abs(ref).max()
+    hi, lo = got[..., 0], got[..., 1]
+    assert np.all(np.abs(lo) <= np.spacing(np.abs(hi)) / 2)
+    Wi = rng.integers(-3, 4, (N, n)).astype(np.float64)
+    qi = rng.integers(-1000, 1001, (N, T)).astype(np.float64)
+    rbfsl.rbfsl_gather_dot(_t(I, torch.int32), _t(_to_pairs(Wi), torch.float32), _t(_to_pairs(qi), torch.float32),
+                           out, pairs=True)
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got[..., 0].astype(np.float64), np.einsum("ij,ijt->it", Wi, qi[I]))
+    np.testing.assert_array_equal(got[..., 1], 0.0)
 
 
 def _run_ctx(w, precision=rbfsl.FP64, mode=rbfsl.DIRECT, steps=None):
