@@ -216,13 +216,18 @@ int rbfsl_pu_apply(rbfsl_pu *pu, const double *q, int T, const double *p, int64_
  * TF32 high part and an FP32 remainder; hi*hi + hi*lo + lo*hi accumulate in FP32 in tensor
  * memory (the mixed-precision evaluation). c: device N x T of c_dtype (RBFSL_F64 or RBFSL_F32);
  * out: device Nq x T FP32. workspace: device buffer of at least
- * rbfsl_global_eval_tc_workspace_bytes(N, T) bytes, 16-byte aligned (the split, transposed
- * coefficients and an error word); the caller owns it and must not share it between calls
- * that overlap on the GPU. Errors: EINVAL, ECUDA. */
-size_t rbfsl_global_eval_tc_workspace_bytes(int64_t N, int T);
+ * rbfsl_global_eval_tc_workspace_bytes(Nq, N, T) bytes (0 for bad sizes), 16-byte aligned: the
+ * split coefficients in the tensor-core operand layout, the nodes in FP32, the split-K partial
+ * tiles and a status word; the caller owns it and must not share it between calls that overlap
+ * on the GPU. The node range is split across CTAs so that the grid fills the device; the
+ * partial sums are added in a fixed order, so the result is deterministic for a given device.
+ * status: device int32 or NULL; set to RBFSL_ETIMEDOUT if a bounded wait inside the kernel gave
+ * up (out is then unspecified), otherwise left unchanged. Asynchronous on `stream`.
+ * Errors: EINVAL (sizes, kernel, dtype, workspace too small or misaligned), ECUDA. */
+size_t rbfsl_global_eval_tc_workspace_bytes(int64_t Nq, int64_t N, int T);
 int rbfsl_global_eval_tc(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
                          double eps, const void *c, int c_dtype, int T, float *out,
-                         void *workspace, size_t workspace_bytes, void *stream);
+                         void *workspace, size_t workspace_bytes, int32_t *status, void *stream);
 
 /* ================================================================== context (Algorithm 1) */
 typedef struct rbfsl_ctx rbfsl_ctx;
@@ -234,6 +239,7 @@ typedef struct rbfsl_stats {
     int64_t uncovered_points;  /* cumulative EUNCOVERED flags (RBF-PU) */
     double time;               /* model time of the current field */
     size_t device_bytes;       /* device memory held by the context */
+    int64_t device_timeouts;   /* nonzero if a bounded wait in a device kernel gave up */
 } rbfsl_stats;
 
 /* Create a context on `device` whose work is enqueued on `stream` (a cudaStream_t of that

@@ -84,7 +84,10 @@ struct rbfsl_ctx {
     unsigned long long *ctr = nullptr;  // [singular, knn failures]
     // prepared state (global method)
     double *LU = nullptr, *C64 = nullptr, *Q64 = nullptr;
-    float *C32 = nullptr;  // global: FP32 coefficients; RBF-PU: FP32 evaluation (mixed)
+    float *C32 = nullptr;  // RBF-PU: FP32 evaluation (mixed)
+    void *tc_ws = nullptr;     // global, mixed: tensor-core evaluation workspace
+    size_t tc_ws_bytes = 0;
+    int32_t *dev_err = nullptr;  // RBFSL_ETIMEDOUT from a bounded device wait
     int32_t *perm = nullptr, *piv = nullptr;
     int prepared_T = 0;
     // RBF-PU
@@ -142,6 +145,8 @@ void release_prepared(rbfsl_ctx *c) {
     cudaFree(c->W); cudaFree(c->ctr);
     c->xi = nullptr; c->I = c->K = c->Ik = c->status = nullptr; c->W = nullptr; c->ctr = nullptr;
     cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->C32); cudaFree(c->perm); cudaFree(c->piv);
+    cudaFree(c->tc_ws); cudaFree(c->dev_err);
+    c->tc_ws = nullptr; c->tc_ws_bytes = 0; c->dev_err = nullptr;
     if (c->pu) rbfsl_pu_destroy(c->pu);
     c->pu = nullptr;
     c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
@@ -179,9 +184,12 @@ int prepare_global(rbfsl_ctx *c) {
     if ((rc = dalloc(c, &c->C64, N * T * sizeof(double)))) return rc;
     if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
     CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+    if ((rc = dalloc(c, &c->dev_err, sizeof(int32_t)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int32_t), c->stream));
     if (c->precision == RBFSL_MIXED) {
         if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
-        if ((rc = dalloc(c, &c->C32, N * T * sizeof(float)))) return rc;
+        c->tc_ws_bytes = global_eval_tc_workspace(N, N, (int)T);
+        if ((rc = dalloc(c, &c->tc_ws, c->tc_ws_bytes))) return rc;
     }
     CTX_RC(c, global_factor_full(c->X, N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
     c->prepared_T = c->T;
@@ -199,14 +207,13 @@ int one_step_global(rbfsl_ctx *c) {
         CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T, RBFSL_F64,
                                      c->q_next, RBFSL_F64, c->stream));
     } else {
-        // FP64 solve of the field (FP32 pairs widened), FP32 evaluation into the freed FP64
-        // right-hand side buffer, stored back as pairs
+        // FP64 solve of the field (FP32 pairs widened); evaluation on the tensor cores (split
+        // TF32, FP32 accumulation) into the freed FP64 right-hand side buffer, stored as pairs
         from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, c->Q64, NT);
         CTX_RC(c, global_solve(c->LU, c->perm, N, c->Q64, c->T, c->C64, c->stream));
-        convert_kernel<double, float><<<blocks, 256, 0, c->stream>>>(c->C64, c->C32, NT);
         float *q32 = reinterpret_cast<float *>(c->Q64);
-        CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C32, c->T, RBFSL_F32,
-                                     q32, RBFSL_F32, c->stream));
+        CTX_RC(c, launch_global_eval_tc(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, RBFSL_F64, c->T, q32,
+                                        c->tc_ws, c->dev_err, c->stream));
         to_pair_kernel<float><<<blocks, 256, 0, c->stream>>>(q32, (float2 *)c->q_next, NT);
         CTX_RC(c, launch_status("global step (mixed)"));
     }
@@ -606,6 +613,11 @@ int rbfsl_get_stats(rbfsl_ctx *c, rbfsl_stats *out) {
         out->singular_points = (int64_t)h[0];
         out->knn_failures = (int64_t)h[1];
         out->uncovered_points = (int64_t)h[2];
+    }
+    if (c->dev_err) {
+        int32_t e = 0;
+        CTX_TRY(c, cudaMemcpy(&e, c->dev_err, sizeof(e), cudaMemcpyDeviceToHost));
+        out->device_timeouts = e != 0;
     }
     out->steps_done = c->steps_done;
     out->time = c->t;

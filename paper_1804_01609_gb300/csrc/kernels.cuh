@@ -105,5 +105,9 @@ int global_solve(const double *LU, const int32_t *perm, int64_t N, const double 
 int launch_global_eval(const double *P, int64_t Nq, const double *X, int64_t N, int kind,
                        double eps, const void *C, int T, int dtype, void *out, int out_dtype,
                        cudaStream_t s);
+size_t global_eval_tc_workspace(int64_t Nq, int64_t N, int T);
+int launch_global_eval_tc(const double *P, int64_t Nq, const double *X, int64_t N, int kind, double eps,
+                          const void *C, int c_dtype, int T, float *out, void *workspace, int32_t *status,
+                          cudaStream_t s);
 
 }  // namespace rbfsl

@@ -47,7 +47,8 @@ _D = ctypes.c_double
 class Stats(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int64), ("singular_points", ctypes.c_int64),
                 ("knn_failures", ctypes.c_int64), ("uncovered_points", ctypes.c_int64),
-                ("time", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("time", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("device_timeouts", ctypes.c_int64)]
 
 
 SIGNATURES = {
@@ -63,8 +64,8 @@ SIGNATURES = {
     "rbfsl_global_factor_noalloc": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
-    "rbfsl_global_eval_tc_workspace_bytes": (ctypes.c_size_t, [_I64, _I]),
-    "rbfsl_global_eval_tc": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P, ctypes.c_size_t, _P]),
+    "rbfsl_global_eval_tc_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
+    "rbfsl_global_eval_tc": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P, ctypes.c_size_t, _P, _P]),
     "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
     "rbfsl_pu_destroy": (_I, [_P]),
     "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
@@ -434,17 +435,17 @@ class Server:
             pass
 
 
-def rbfsl_global_eval_tc(p, x, kernel, eps, c, out, workspace=None, stream=None):
+def rbfsl_global_eval_tc(p, x, kernel, eps, c, out, workspace=None, status=None, stream=None):
     """Tensor-core (split TF32) evaluation; workspace: a uint8 device tensor (allocated here
-    when None)."""
+    when None); status: an int32 device tensor of one element or None."""
     import torch
     T = c.shape[1] if c.dim() == 2 else 1
-    need = load().rbfsl_global_eval_tc_workspace_bytes(x.shape[0], T)
+    need = load().rbfsl_global_eval_tc_workspace_bytes(p.shape[0], x.shape[0], T)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=c.device)
     _check(load().rbfsl_global_eval_tc(_ptr(p), p.shape[0], _ptr(x), x.shape[0], kernel, float(eps),
                                        _ptr(c), _dtype_code(c), T, _ptr(out), _ptr(workspace),
-                                       workspace.numel(), _stream(stream)))
+                                       workspace.numel(), _ptr(status), _stream(stream)))
     return workspace
 
 

@@ -19,19 +19,51 @@ def _t(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dtype)
 
 
-@pytest.mark.parametrize("Nq,N,T", [(128, 32, 32), (300, 1000, 5), (777, 2562, 64), (1, 40, 1)])
-def test_tc_eval_parity(orc, Nq, N, T):
+def _phi(P, X, kind, eps):
+    d2 = ((P[:, None, :] - X[None]) ** 2).sum(-1)
+    return np.exp(-(eps ** 2) * d2) if kind == rbfsl.GAUSS else 1.0 / np.sqrt(1.0 + eps ** 2 * d2)
+
+
+# sizes: one tile; ragged points and nodes (partial 128-point tile, partial 32-node chunk);
+# split node ranges; Tn = 112 (one CTA per SM); two tracer tiles (T = 300 -> 2 x 160); one point
+@pytest.mark.parametrize("Nq,N,T,kind", [(128, 32, 32, rbfsl.GAUSS), (300, 1000, 5, rbfsl.GAUSS),
+                                         (777, 2562, 64, rbfsl.GAUSS), (1, 40, 1, rbfsl.GAUSS),
+                                         (200, 3001, 100, rbfsl.GAUSS), (130, 700, 300, rbfsl.GAUSS),
+                                         (513, 1500, 17, rbfsl.IMQ)])
+def test_tc_eval_parity(orc, Nq, N, T, kind):
     X = inputs.nodes(N, 9)
     rng = np.random.default_rng(N + T)
     C = rng.standard_normal((N, T))
     P = inputs.random_unit_vectors(Nq, rng)
-    ref = orc.global_eval(P, X, C, orc.GAUSS, EPS)
-    scale = np.exp(-(EPS ** 2) * ((P[:, None, :] - X[None]) ** 2).sum(-1)) @ np.abs(C)
+    ref = orc.global_eval(P, X, C, orc.GAUSS if kind == rbfsl.GAUSS else orc.IMQ, EPS)
+    scale = _phi(P, X, kind, EPS) @ np.abs(C)
     out = torch.full((Nq, T), float("nan"), dtype=torch.float32, device=DEV)
-    rbfsl.rbfsl_global_eval_tc(_t(P), _t(X), rbfsl.GAUSS, EPS, _t(C), out)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    rbfsl.rbfsl_global_eval_tc(_t(P), _t(X), kind, EPS, _t(C), out, status=st)
     got = out.cpu().numpy().astype(np.float64)
+    assert int(st.item()) == 0
     assert np.isfinite(got).all()
     assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-30)
+
+
+def test_tc_eval_deterministic_and_workspace_checked():
+    """Split-K partial sums are added in a fixed order: two calls agree bit for bit. A workspace
+    below the stated size is refused (EINVAL) before any launch."""
+    N, T, Nq = 4000, 64, 2000
+    X = inputs.nodes(N, 5)
+    rng = np.random.default_rng(1)
+    P, C = _t(inputs.random_unit_vectors(Nq, rng)), _t(rng.standard_normal((N, T)))
+    x = _t(X)
+    o1 = torch.empty((Nq, T), dtype=torch.float32, device=DEV)
+    o2 = torch.empty_like(o1)
+    ws = rbfsl.rbfsl_global_eval_tc(P, x, rbfsl.GAUSS, EPS, C, o1)
+    rbfsl.rbfsl_global_eval_tc(P, x, rbfsl.GAUSS, EPS, C, o2, workspace=ws)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
+    small = torch.empty(ws.numel() - 16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(rbfsl.RbfslError) as e:
+        rbfsl.rbfsl_global_eval_tc(P, x, rbfsl.GAUSS, EPS, C, o1, workspace=small)
+    assert e.value.code == rbfsl.EINVAL
 
 
 def test_tc_eval_full_size_sampled(orc):
