@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
-    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq"],
+    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq", "tceval"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
     ap.add_argument("--repeat", type=int, default=3)
@@ -527,6 +527,26 @@ def run_case(args):
         r = bench_wq_hbm(rbfsl, torch, stream, flush, K=args.repeat)
         print(f"case wq: {json.dumps(r)}", flush=True)
         return
+    if args.case == "tceval":  # the tensor-core global evaluation at the global workload's size
+        from paper_1804_01609_gb300 import inputs
+        wg = inputs.config_global_rotation()
+        xg = torch.as_tensor(wg.X, device="cuda")
+        pg = torch.empty_like(xg)
+        rbfsl.rbfsl_trace_rk4(xg, wg.vel_kind, wg.vel_params, wg.dt, wg.dt, rbfsl.FP64, pg)
+        g = torch.Generator(device="cuda").manual_seed(11)
+        C = torch.randn((wg.N, wg.T), generator=g, device="cuda", dtype=torch.float64)
+        o = torch.empty((wg.N, wg.T), dtype=torch.float32, device="cuda")
+        ws = rbfsl.rbfsl_global_eval_tc(pg, xg, rbfsl.GAUSS, wg.eps, C, o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.repeat):
+            rbfsl.rbfsl_global_eval_tc(pg, xg, rbfsl.GAUSS, wg.eps, C, o, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"case tceval: {e0.elapsed_time(e1) / args.repeat:.3f} ms per call (N = Nq = {wg.N}, T = {wg.T})",
+              flush=True)
+        return
     w = workload()
     N, n = w.N, w.n
     nq = min(args.nq, N)
@@ -684,7 +704,8 @@ def main():
             center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
     wq = bench_wq_hbm(rbfsl, torch, stream, flush)
-    glob = bench_global(rbfsl, torch, stream, flush)
+    glob = bench_global(rbfsl, torch, stream, flush,
+                        accuracy_eps=(6.0, 9.0, 24.0) if args.accuracy_steps > 0 else ())
     glob["evaluation_alone"] = bench_global_eval(rbfsl, torch, stream, flush)
     batched = {}
     if not args.no_batched:
