@@ -57,9 +57,13 @@ __global__ void __launch_bounds__(256) gather_dot_kernel(const int32_t *__restri
 
 // Vectorised variant for T a multiple of the vector width V (4 floats or 2 doubles = 16 B):
 // a row group of G = T / V lanes serves one row (32 / G rows per warp), every lane owning V
-// consecutive tracers, so each gathered q row is read as G 16-byte pieces; (w, idx) come in
-// chunks of G, one per lane, and are broadcast by shuffles. Same summation order as the
-// scalar kernel (j ascending, one fma per term).
+// consecutive tracers, so each gathered q row is read as G 16-byte pieces. Members are taken in
+// batches of kGatherBatch: the batch's indices and weights are loaded first (the G lanes of a
+// row group read the same words), then all its q pieces are requested before the first is
+// used, so a lane keeps kGatherBatch gathers in flight instead of one. Same summation order as
+// the scalar kernel (j ascending, one fma per term).
+constexpr int kGatherBatch = 8;
+
 template <typename R, typename RV, int V, bool kDiff>
 __global__ void __launch_bounds__(256) gather_dot_vec_kernel(const int32_t *__restrict__ idx,
                                                              const R *__restrict__ W, int64_t Nq,
@@ -70,55 +74,57 @@ __global__ void __launch_bounds__(256) gather_dot_vec_kernel(const int32_t *__re
     const int rows_per_warp = kWarp / G;
     const int sub = lane % G, grp = lane / G;
     const int64_t i = gwarp * rows_per_warp + grp;
-    const bool active = grp < rows_per_warp && i < Nq;
-    if (__all_sync(0xffffffffu, !active)) return;
+    if (grp >= rows_per_warp || i >= Nq) return;
     const RV *qv = reinterpret_cast<const RV *>(q);
     const int Tv = T / V;
+    const int32_t *Ir = idx + i * n;
+    const R *Wr = W + i * n;
     R acc[V], qc[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) { acc[v] = R(0); qc[v] = R(0); }
-    if (kDiff && active) {
-        const int c = idx[i * n];
+    if (kDiff) {
+        const int c = Ir[0];
         const RV x = c >= 0 ? qv[(int64_t)c * Tv + sub] : RV{};
         const R *xr = reinterpret_cast<const R *>(&x);
 #pragma unroll
         for (int v = 0; v < V; ++v) qc[v] = c >= 0 ? xr[v] : R(NAN);
     }
-    for (int j0 = 0; j0 < n; j0 += G) {
-        R wj = R(0);
-        int sj = 0;
-        if (active && j0 + sub < n) {
-            wj = W[i * n + j0 + sub];
-            sj = idx[i * n + j0 + sub];
-        }
-        const int cnt = min(G, n - j0);
-        for (int jj = 0; jj < cnt; ++jj) {
-            const R w = __shfl_sync(0xffffffffu, wj, (lane / G) * G + jj);
-            const int s = __shfl_sync(0xffffffffu, sj, (lane / G) * G + jj);
-            if (active) {
-                const RV x = s >= 0 ? qv[(int64_t)s * Tv + sub] : RV{};
-                const R *xr = reinterpret_cast<const R *>(&x);
+    auto term = [&](R w, int sidx, const RV &x) {
+        const R *xr = reinterpret_cast<const R *>(&x);
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const R val = s >= 0 ? xr[v] : R(NAN);
-                    acc[v] = fma(w, kDiff ? (val - qc[v]) : val, acc[v]);
-                }
-            }
+        for (int v = 0; v < V; ++v) {
+            const R val = sidx >= 0 ? xr[v] : R(NAN);  // failed stencil
+            acc[v] = fma(w, kDiff ? (val - qc[v]) : val, acc[v]);
         }
-    }
-    if (active) {
-        RV o;
-        R *orr = reinterpret_cast<R *>(&o);
+    };
+    int j0 = 0;
+    for (; j0 + kGatherBatch <= n; j0 += kGatherBatch) {
+        int sb[kGatherBatch];
+        R wb[kGatherBatch];
+        RV xb[kGatherBatch];
 #pragma unroll
-        for (int v = 0; v < V; ++v) orr[v] = kDiff ? qc[v] + acc[v] : acc[v];
-        reinterpret_cast<RV *>(out)[i * Tv + sub] = o;
+        for (int b = 0; b < kGatherBatch; ++b) { sb[b] = Ir[j0 + b]; wb[b] = Wr[j0 + b]; }
+#pragma unroll
+        for (int b = 0; b < kGatherBatch; ++b) xb[b] = sb[b] >= 0 ? qv[(int64_t)sb[b] * Tv + sub] : RV{};
+#pragma unroll
+        for (int b = 0; b < kGatherBatch; ++b) term(wb[b], sb[b], xb[b]);
     }
+    for (; j0 < n; ++j0) {
+        const int sidx = Ir[j0];
+        term(Wr[j0], sidx, sidx >= 0 ? qv[(int64_t)sidx * Tv + sub] : RV{});
+    }
+    RV o;
+    R *orr = reinterpret_cast<R *>(&o);
+#pragma unroll
+    for (int v = 0; v < V; ++v) orr[v] = kDiff ? qc[v] + acc[v] : acc[v];
+    reinterpret_cast<RV *>(out)[i * Tv + sub] = o;
 }
 
 // FP32 pairs (mixed precision): weights and field stored as (hi, lo) pairs and the sum
 // formed in pair arithmetic (pair_fma), FP32 operations only. Each lane owns V consecutive
 // tracers (V = 2: one 16-byte load per gathered row piece; V = 1 for odd T); a row group of G
-// lanes covers G * V tracers per pass. Same element order (j ascending) as the batched path.
+// lanes covers G * V tracers per pass. Members in batches of kGatherBatch as in
+// gather_dot_vec_kernel. Same element order (j ascending) as the batched path.
 template <int V>
 __global__ void __launch_bounds__(256) gather_dot_pair_kernel(const int32_t *__restrict__ idx,
                                                               const float2 *__restrict__ W, int64_t Nq,
@@ -130,42 +136,42 @@ __global__ void __launch_bounds__(256) gather_dot_pair_kernel(const int32_t *__r
     const int rows_per_warp = kWarp / G;
     const int sub = lane % G, grp = lane / G;
     const int64_t i = gwarp * rows_per_warp + grp;
-    const bool active = i < Nq;
-    if (__all_sync(0xffffffffu, !active)) return;
+    if (grp >= rows_per_warp || i >= Nq) return;
+    const int32_t *Ir = idx + i * n;
+    const float2 *Wr = W + i * n;
     for (int t0 = 0; t0 < T; t0 += G * V) {
         const int t = t0 + sub * V;
-        const bool tv = active && t < T;  // V = 2 only for even T, so t + 1 < T too
+        if (t >= T) continue;  // V = 2 only for even T, so t + 1 < T too
         float sh[V], sl[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) { sh[v] = 0.f; sl[v] = 0.f; }
-        for (int j0 = 0; j0 < n; j0 += G) {
-            float2 wj = make_float2(0.f, 0.f);
-            int sj = 0;
-            if (active && j0 + sub < n) {
-                wj = W[i * n + j0 + sub];
-                sj = idx[i * n + j0 + sub];
-            }
-            const int cnt = min(G, n - j0);
-            for (int jj = 0; jj < cnt; ++jj) {
-                const int src = grp * G + jj;
-                const float2 w = make_float2(__shfl_sync(0xffffffffu, wj.x, src), __shfl_sync(0xffffffffu, wj.y, src));
-                const int sidx = __shfl_sync(0xffffffffu, sj, src);
-                if (tv) {
-                    const Vec x = sidx >= 0 ? *reinterpret_cast<const Vec *>(q + (int64_t)sidx * T + t) : Vec{};
-                    const float2 *xp = reinterpret_cast<const float2 *>(&x);
+        auto term = [&](float2 w, int sidx, const Vec &x) {
+            const float2 *xp = reinterpret_cast<const float2 *>(&x);
 #pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        pair_fma(w, sidx >= 0 ? xp[v] : make_float2(NAN, NAN), sh[v], sl[v]);
-                }
-            }
-        }
-        if (tv) {
-            Vec o;
-            float2 *op = reinterpret_cast<float2 *>(&o);
+            for (int v = 0; v < V; ++v) pair_fma(w, sidx >= 0 ? xp[v] : make_float2(NAN, NAN), sh[v], sl[v]);
+        };
+        int j0 = 0;
+        for (; j0 + kGatherBatch <= n; j0 += kGatherBatch) {
+            int sb[kGatherBatch];
+            float2 wb[kGatherBatch];
+            Vec xb[kGatherBatch];
 #pragma unroll
-            for (int v = 0; v < V; ++v) op[v] = pair_norm(sh[v], sl[v]);
-            *reinterpret_cast<Vec *>(out + i * T + t) = o;
+            for (int b = 0; b < kGatherBatch; ++b) { sb[b] = Ir[j0 + b]; wb[b] = Wr[j0 + b]; }
+#pragma unroll
+            for (int b = 0; b < kGatherBatch; ++b)
+                xb[b] = sb[b] >= 0 ? *reinterpret_cast<const Vec *>(q + (int64_t)sb[b] * T + t) : Vec{};
+#pragma unroll
+            for (int b = 0; b < kGatherBatch; ++b) term(wb[b], sb[b], xb[b]);
         }
+        for (; j0 < n; ++j0) {
+            const int sidx = Ir[j0];
+            term(Wr[j0], sidx, sidx >= 0 ? *reinterpret_cast<const Vec *>(q + (int64_t)sidx * T + t) : Vec{});
+        }
+        Vec o;
+        float2 *op = reinterpret_cast<float2 *>(&o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) op[v] = pair_norm(sh[v], sl[v]);
+        *reinterpret_cast<Vec *>(out + i * T + t) = o;
     }
 }
 
