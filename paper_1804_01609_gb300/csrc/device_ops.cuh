@@ -290,9 +290,116 @@ __device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, 
 }
 
 
+// Trailing update of step k for the rows at list positions p0, p0 + NW, ... < m of the row list L
+// (rows are not moved; L orders them as the swaps of partial pivoting would): A[r][j] -= A[r][k] *
+// A[L[k]][j] for the NCH column chunks j = j0 + lane + 32c <= m. Same operand pipelining and
+// the same FMA per element as trailing_update.
+template <int NW, int NCH>
+__device__ __forceinline__ void trailing_update_list(double *__restrict__ A, int ld, int m, int k, int j0,
+                                                     const int *__restrict__ L, int p, int lane) {
+    const int prow = L[k];
+    double pk[NCH];
+    int jc[NCH];
+    bool on[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        jc[c] = j0 + lane + c * kWarp;
+        on[c] = jc[c] <= m;
+        pk[c] = on[c] ? A[prow * ld + jc[c]] : 0.0;
+    }
+    if (p + NW < m) {
+        int r0 = L[p], r1 = L[p + NW];
+        double l0 = A[r0 * ld + k], l1 = A[r1 * ld + k];
+        double v0[NCH], v1[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) {
+            v0[c] = on[c] ? A[r0 * ld + jc[c]] : 0.0;
+            v1[c] = on[c] ? A[r1 * ld + jc[c]] : 0.0;
+        }
+        for (;;) {
+            const int pn = p + 2 * NW;
+            const bool more = pn + NW < m;
+            int n0 = 0, n1 = 0;
+            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
+            if (more) {
+                n0 = L[pn];
+                n1 = L[pn + NW];
+                nl0 = A[n0 * ld + k];
+                nl1 = A[n1 * ld + k];
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                nv0[c] = (more && on[c]) ? A[n0 * ld + jc[c]] : 0.0;
+                nv1[c] = (more && on[c]) ? A[n1 * ld + jc[c]] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                if (c < NCH - 1 || on[c]) {
+                    A[r0 * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
+                    A[r1 * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
+                }
+            }
+            p = pn;
+            if (!more) break;
+            r0 = n0;
+            r1 = n1;
+            l0 = nl0;
+            l1 = nl1;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                v0[c] = nv0[c];
+                v1[c] = nv1[c];
+            }
+        }
+    }
+    if (p < m) {
+        const int r = L[p];
+        const double l0 = A[r * ld + k];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c)
+            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
+    }
+}
+
+// Pivot of column k by one warp, rows at positions k..m-1 of list cur: the largest |a_rk|
+// (integer compare of the magnitude bits), the smaller position on a tie. Writes the list with
+// positions k and the pivot's swapped to nxt[k..m-1], the inverse pivot to invp[k] and the
+// multipliers a_rk / a_pk to column k of the remaining rows; *flag = 2 for a zero, infinite or
+// NaN pivot.
+__device__ __forceinline__ void pivot_step(double *__restrict__ A, int ld, int m, int k, const int *__restrict__ cur,
+                                           int *__restrict__ nxt, double *__restrict__ invp, int *flag, int lane) {
+    long long best = -1;
+    int bpos = m;
+    for (int p = k + lane; p < m; p += kWarp) {
+        const long long v = __double_as_longlong(A[cur[p] * ld + k]) & 0x7fffffffffffffffLL;
+        if (v > best) { best = v; bpos = p; }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bpos, off);
+        if (ob > best || (ob == best && oi < bpos)) { best = ob; bpos = oi; }
+    }
+    if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
+        if (lane == 0) *flag = 2;
+        return;
+    }
+    for (int p = k + lane; p < m; p += kWarp) nxt[p] = p == k ? cur[bpos] : (p == bpos ? cur[k] : cur[p]);
+    __syncwarp();
+    const int prow = nxt[k];
+    double inv = 0.0;
+    if (lane == 0) {
+        inv = 1.0 / A[prow * ld + k];
+        invp[k] = inv;
+    }
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    for (int p = k + 1 + lane; p < m; p += kWarp) A[nxt[p] * ld + k] *= inv;
+}
+
 // Shared-memory layout of one point: A (m x ld, the augmented [A~ | b] system), the stencil
-// coordinates (3 x n), the inverse pivots (m), one flag word.
-__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + m + 1; }
+// coordinates (3 x n; after assembly the solution buffer), the inverse pivots (m), a flag word
+// and two row lists of m ints (multi-warp elimination).
+__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + 2 * m + 1; }
 
 // Weights of one point by a group of NW warps (thread t of the group, NW * 32 threads):
 // assemble [[A, P], [P^T, 0] | phi(|p - x_j|); Y(p)] (Eqs. rbf_poly, rbf_poly_linsys) in the
@@ -350,7 +457,73 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
     if (t == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
     gsync();
 
-    // ---- Gaussian elimination with partial pivoting on [A~ | b]
+    if constexpr (NW > 1 && NW % 4 == 1) {
+        // ---- Gaussian elimination with partial pivoting on [A~ | b], look-ahead form with a
+        // pivot warp. Rows stay in place; a row list gives the order that the row swaps would.
+        // While warps 1..NW-1 (a multiple of four: one per SM sub-partition) apply step k to the
+        // columns k+2..m, warp 0 applies it to column k+1, finds the pivot of step k+1 and forms
+        // its multipliers, so that the pivot search and the division run beside the DFMAs (one
+        // barrier per step). Every element receives the same FMAs, and the pivots are the same
+        // (ties to the smaller position), as with swapped rows.
+        constexpr int NT = NW - 1;
+        int *L0 = flag + 2, *L1 = L0 + m;
+        if (warp == 0) {
+            for (int p = lane; p < m; p += kWarp) L0[p] = p;
+            __syncwarp();
+            pivot_step(A, ld, m, 0, L0, L1, invp, flag, lane);
+        }
+        __syncthreads();
+        if (*flag) return RBFSL_ESINGULAR;
+        int *L = L1, *Ln = L0;
+        for (int k = 0; k < m; ++k) {
+            if (warp == 0 && k + 1 < m) {
+                const int prow = L[k];
+                const double u = A[prow * ld + k + 1];
+                for (int p = k + 1 + lane; p < m; p += kWarp) {
+                    const int r = L[p];
+                    A[r * ld + k + 1] = fma(-A[r * ld + k], u, A[r * ld + k + 1]);
+                }
+                for (int p = lane; p <= k; p += kWarp) Ln[p] = L[p];  // fixed pivot positions
+                __syncwarp();
+                pivot_step(A, ld, m, k + 1, L, Ln, invp, flag, lane);
+            }
+            if (warp > 0 && k + 2 <= m) {
+                const int p0 = k + warp;  // position k + 1 + (warp - 1)
+                switch ((m - k - 1 + kWarp - 1) / kWarp) {
+                    case 1: trailing_update_list<NT, 1>(A, ld, m, k, k + 2, L, p0, lane); break;
+                    case 2: trailing_update_list<NT, 2>(A, ld, m, k, k + 2, L, p0, lane); break;
+                    case 3: trailing_update_list<NT, 3>(A, ld, m, k, k + 2, L, p0, lane); break;
+                    case 4: trailing_update_list<NT, 4>(A, ld, m, k, k + 2, L, p0, lane); break;
+                    default: trailing_update_list<NT, 5>(A, ld, m, k, k + 2, L, p0, lane); break;
+                }
+            }
+            __syncthreads();
+            if (*flag) return RBFSL_ESINGULAR;
+            if (k + 1 < m) {
+                int *tmp = L;
+                L = Ln;
+                Ln = tmp;
+            }
+        }
+        if (warp != 0) return RBFSL_OK;
+        // ---- back substitution on the rhs column (warp 0), pivot rows in list order, the
+        // solution gathered in the (no longer needed) coordinate buffer, then stored in column m
+        double *xs = cx;
+        for (int r = m - 1; r >= 0; --r) {
+            const double xr = A[L[r] * ld + m] * invp[r];
+            __syncwarp();
+            if (lane == 0) xs[r] = xr;
+            for (int s2 = lane; s2 < r; s2 += kWarp) {
+                const int q = L[s2];
+                A[q * ld + m] = fma(-A[q * ld + r], xr, A[q * ld + m]);
+            }
+            __syncwarp();
+        }
+        for (int r = lane; r < m; r += kWarp) A[r * ld + m] = xs[r];
+        __syncwarp();
+        return RBFSL_OK;
+    } else {
+    // ---- Gaussian elimination with partial pivoting on [A~ | b] (one warp: rows swapped)
     for (int k = 0; k < m; ++k) {
         if (warp == 0) {
             // pivot: largest |a_rk| (integer compare of the magnitude bits), smaller row on a tie
@@ -405,6 +578,7 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
         __syncwarp();
     }
     return RBFSL_OK;
+    }
 }
 
 // Centre-stencil weights of one point by one warp (Sec. 3.3): the point uses the stencil

@@ -62,10 +62,11 @@ struct WeightsArgs {
     int32_t *status;
 };
 
-// NW warps per point (1, 4 or 8). With NW = 1 a block holds blockDim/32 independent points and
+// NW warps per point (1, 4, 5, 8 or 9). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW > 1 a block is one point and uses __syncthreads.
+// NW = 5 or 9: four or eight warps for the trailing updates and a pivot warp (look-ahead).
 template <int NW, typename WT>
-__global__ void __launch_bounds__(NW == 8 ? 256 : 128) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
+__global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
     extern __shared__ double smem[];
     constexpr int GT = NW * kWarp;
     const int g = threadIdx.x / GT, t = threadIdx.x % GT;
@@ -112,14 +113,19 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     const int bytes = a.stencil_doubles * 8;
     if (bytes > 40 * 1024) {
         // large systems (m >~ 70): several warps per point so that every SM sub-partition's
-        // FP64 unit is fed although only one or two points fit in shared memory.
-        // RBFSL_WEIGHTS_WARPS=8 selects eight warps per point (default four).
+        // FP64 unit is fed although only one or two points fit in shared memory. Default: eight
+        // warps of trailing updates plus a pivot warp (look-ahead; 288 threads, two points per
+        // SM); RBFSL_WEIGHTS_WARPS=5 selects four plus the pivot warp, 4 or 8 that many warps
+        // with the pivot search between the updates.
         static const int nw = [] {
             const char *e = getenv("RBFSL_WEIGHTS_WARPS");
-            return (e && atoi(e) == 8) ? 8 : 4;
+            const int v = e ? atoi(e) : 9;
+            return (v == 4 || v == 5 || v == 8) ? v : 9;
         }();
+        if (nw == 9) return launch_weights_typed<9>(a, 1, w, w_dtype, s);
         if (nw == 8) return launch_weights_typed<8>(a, 1, w, w_dtype, s);
-        return launch_weights_typed<4>(a, 1, w, w_dtype, s);
+        if (nw == 4) return launch_weights_typed<4>(a, 1, w, w_dtype, s);
+        return launch_weights_typed<5>(a, 1, w, w_dtype, s);
     }
     return launch_weights_typed<1>(a, 4, w, w_dtype, s);  // four independent points (warps) per block
 }
