@@ -131,7 +131,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
 # capture of this kernel version (profiles/weights_direct_N40962_n84.md).
-WEIGHTS_DRAM_BYTES = 16.27e6
+WEIGHTS_DRAM_BYTES = 16.26e6
 
 
 def weights_flops(m):
@@ -743,7 +743,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 GEPP, m = 109)",
+        "roofline": {"bound": "alu", "kernel": "weights_kernel<9, float2> (FP64 GEPP, look-ahead, m = 109)",
                      "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": WEIGHTS_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",
