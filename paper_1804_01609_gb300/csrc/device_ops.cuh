@@ -361,6 +361,52 @@ __device__ __forceinline__ void trailing_update_list(double *__restrict__ A, int
     }
 }
 
+// Trailing update of step k, flattened: the warp's rows (list positions p0, p0 + NT, ... < m)
+// times the columns j0..m form one index space that the 32 lanes walk in consecutive chunks,
+// so that only the last chunk of the step has idle lanes (a per-row chunking leaves the last
+// chunk of every row partly idle, and an idle lane of a DFMA still costs FP64 pipe time). Per
+// element the multiplier, the pivot-row value and the element are loaded from shared memory;
+// two chunks are loaded before either is stored. Same FMA per element as trailing_update.
+__device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int ld, int m, int k, int j0,
+                                                     const int *__restrict__ L, int p0, int NT, int lane) {
+    if (p0 >= m) return;
+    const int C = m - j0 + 1;
+    const int R = (m - 1 - p0) / NT + 1;
+    const int E = R * C;
+    const int prow = L[k];
+    const int q = kWarp / C, rem = kWarp - q * C;  // a step of 32 elements: q rows and rem columns
+    int rr = lane / C, cc = lane - (lane / C) * C;
+    auto advance = [&](int &r_, int &c_) {
+        r_ += q;
+        c_ += rem;
+        if (c_ >= C) { c_ -= C; ++r_; }
+    };
+    int base = 0;
+    for (; base + kWarp < E; base += 2 * kWarp) {
+        // chunk base (all lanes active) and chunk base + 32 (lanes below E)
+        int r1 = rr, c1 = cc;
+        advance(r1, c1);
+        const bool act1 = base + kWarp + lane < E;
+        const int a0 = L[p0 + rr * NT] * ld, a1 = act1 ? L[p0 + r1 * NT] * ld : 0;
+        const double l0 = A[a0 + k], u0 = A[prow * ld + j0 + cc], v0 = A[a0 + j0 + cc];
+        double l1 = 0.0, u1 = 0.0, v1 = 0.0;
+        if (act1) {
+            l1 = A[a1 + k];
+            u1 = A[prow * ld + j0 + c1];
+            v1 = A[a1 + j0 + c1];
+        }
+        A[a0 + j0 + cc] = fma(-l0, u0, v0);
+        if (act1) A[a1 + j0 + c1] = fma(-l1, u1, v1);
+        rr = r1;
+        cc = c1;
+        advance(rr, cc);
+    }
+    if (base < E && base + lane < E) {
+        const int a0 = L[p0 + rr * NT] * ld;
+        A[a0 + j0 + cc] = fma(-A[a0 + k], A[prow * ld + j0 + cc], A[a0 + j0 + cc]);
+    }
+}
+
 // Pivot of column k by one warp, rows at positions k..m-1 of list cur: the largest |a_rk|
 // (integer compare of the magnitude bits), the smaller position on a tie. Writes the list with
 // positions k and the pivot's swapped to nxt[k..m-1], the inverse pivot to invp[k] and the
@@ -487,16 +533,8 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
                 __syncwarp();
                 pivot_step(A, ld, m, k + 1, L, Ln, invp, flag, lane);
             }
-            if (warp > 0 && k + 2 <= m) {
-                const int p0 = k + warp;  // position k + 1 + (warp - 1)
-                switch ((m - k - 1 + kWarp - 1) / kWarp) {
-                    case 1: trailing_update_list<NT, 1>(A, ld, m, k, k + 2, L, p0, lane); break;
-                    case 2: trailing_update_list<NT, 2>(A, ld, m, k, k + 2, L, p0, lane); break;
-                    case 3: trailing_update_list<NT, 3>(A, ld, m, k, k + 2, L, p0, lane); break;
-                    case 4: trailing_update_list<NT, 4>(A, ld, m, k, k + 2, L, p0, lane); break;
-                    default: trailing_update_list<NT, 5>(A, ld, m, k, k + 2, L, p0, lane); break;
-                }
-            }
+            if (warp > 0 && k + 2 <= m)  // rows at positions k + 1 + (warp - 1), step NT
+                trailing_update_flat(A, ld, m, k, k + 2, L, k + warp, NT, lane);
             __syncthreads();
             if (*flag) return RBFSL_ESINGULAR;
             if (k + 1 < m) {
