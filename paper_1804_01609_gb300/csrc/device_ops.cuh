@@ -224,156 +224,22 @@ __host__ __device__ inline int knn_cap(int k) {
     while (cap < 3 * k) cap <<= 1;
     return cap;
 }
-// Trailing update of one elimination step for the rows r0, r0 + NW, r0 + 2 NW, ... < m:
-// A[r][j] -= A[r][k] * A[k][j] for the NCH column chunks j = k+1+lane+32c <= m. NCH is a
-// compile-time count so that no FP64 instruction is issued for a chunk with no live column
-// (a predicated-off DFMA still takes an FP64 issue slot). Rows go two at a time, and the next
-// pair's operands are loaded before the current pair is stored, so shared-memory latency
-// overlaps the DFMAs.
-template <int NW, int NCH>
-__device__ __forceinline__ void trailing_update(double *__restrict__ A, int ld, int m, int k,
-                                                int r, int lane) {
-    double pk[NCH];
-    int jc[NCH];
-    bool on[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        jc[c] = k + 1 + lane + c * kWarp;
-        on[c] = jc[c] <= m;
-        pk[c] = on[c] ? A[k * ld + jc[c]] : 0.0;
-    }
-    if (r + NW < m) {
-        double l0 = A[r * ld + k], l1 = A[(r + NW) * ld + k];
-        double v0[NCH], v1[NCH];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            v0[c] = on[c] ? A[r * ld + jc[c]] : 0.0;
-            v1[c] = on[c] ? A[(r + NW) * ld + jc[c]] : 0.0;
-        }
-        for (;;) {
-            const int rn = r + 2 * NW;
-            const bool more = rn + NW < m;
-            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
-            if (more) {
-                nl0 = A[rn * ld + k];
-                nl1 = A[(rn + NW) * ld + k];
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                nv0[c] = (more && on[c]) ? A[rn * ld + jc[c]] : 0.0;
-                nv1[c] = (more && on[c]) ? A[(rn + NW) * ld + jc[c]] : 0.0;
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (c < NCH - 1 || on[c]) {
-                    A[r * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
-                    A[(r + NW) * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
-                }
-            }
-            r = rn;
-            if (!more) break;
-            l0 = nl0;
-            l1 = nl1;
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                v0[c] = nv0[c];
-                v1[c] = nv1[c];
-            }
-        }
-    }
-    if (r < m) {
-        const double l0 = A[r * ld + k];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c)
-            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
-    }
-}
-
-
-// Trailing update of step k for the rows at list positions p0, p0 + NW, ... < m of the row list L
-// (rows are not moved; L orders them as the swaps of partial pivoting would): A[r][j] -= A[r][k] *
-// A[L[k]][j] for the NCH column chunks j = j0 + lane + 32c <= m. Same operand pipelining and
-// the same FMA per element as trailing_update.
-template <int NW, int NCH>
-__device__ __forceinline__ void trailing_update_list(double *__restrict__ A, int ld, int m, int k, int j0,
-                                                     const int *__restrict__ L, int p, int lane) {
-    const int prow = L[k];
-    double pk[NCH];
-    int jc[NCH];
-    bool on[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        jc[c] = j0 + lane + c * kWarp;
-        on[c] = jc[c] <= m;
-        pk[c] = on[c] ? A[prow * ld + jc[c]] : 0.0;
-    }
-    if (p + NW < m) {
-        int r0 = L[p], r1 = L[p + NW];
-        double l0 = A[r0 * ld + k], l1 = A[r1 * ld + k];
-        double v0[NCH], v1[NCH];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            v0[c] = on[c] ? A[r0 * ld + jc[c]] : 0.0;
-            v1[c] = on[c] ? A[r1 * ld + jc[c]] : 0.0;
-        }
-        for (;;) {
-            const int pn = p + 2 * NW;
-            const bool more = pn + NW < m;
-            int n0 = 0, n1 = 0;
-            double nl0 = 0.0, nl1 = 0.0, nv0[NCH], nv1[NCH];
-            if (more) {
-                n0 = L[pn];
-                n1 = L[pn + NW];
-                nl0 = A[n0 * ld + k];
-                nl1 = A[n1 * ld + k];
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                nv0[c] = (more && on[c]) ? A[n0 * ld + jc[c]] : 0.0;
-                nv1[c] = (more && on[c]) ? A[n1 * ld + jc[c]] : 0.0;
-            }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (c < NCH - 1 || on[c]) {
-                    A[r0 * ld + jc[c]] = fma(-l0, pk[c], v0[c]);
-                    A[r1 * ld + jc[c]] = fma(-l1, pk[c], v1[c]);
-                }
-            }
-            p = pn;
-            if (!more) break;
-            r0 = n0;
-            r1 = n1;
-            l0 = nl0;
-            l1 = nl1;
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                v0[c] = nv0[c];
-                v1[c] = nv1[c];
-            }
-        }
-    }
-    if (p < m) {
-        const int r = L[p];
-        const double l0 = A[r * ld + k];
-#pragma unroll
-        for (int c = 0; c < NCH; ++c)
-            if (c < NCH - 1 || on[c]) A[r * ld + jc[c]] = fma(-l0, pk[c], A[r * ld + jc[c]]);
-    }
-}
-
 // Trailing update of step k, flattened: the warp's rows (list positions p0, p0 + NT, ... < m)
 // times the columns j0..m form one index space that the 32 lanes walk in consecutive chunks,
 // so that only the last chunk of the step has idle lanes (a per-row chunking leaves the last
 // chunk of every row partly idle, and an idle lane of a DFMA still costs FP64 pipe time). Per
 // element the multiplier, the pivot-row value and the element are loaded from shared memory;
 // two chunks are loaded before either is stored. Same FMA per element as trailing_update.
+// With kList false the rows are in place (position = row, pivot row k), L unused.
+template <bool kList>
 __device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int ld, int m, int k, int j0,
                                                      const int *__restrict__ L, int p0, int NT, int lane) {
     if (p0 >= m) return;
     const int C = m - j0 + 1;
     const int R = (m - 1 - p0) / NT + 1;
     const int E = R * C;
-    const int prow = L[k];
+    const int prow = kList ? L[k] : k;
+    auto row_of = [&](int pos) { return kList ? L[pos] : pos; };
     const int q = kWarp / C, rem = kWarp - q * C;  // a step of 32 elements: q rows and rem columns
     int rr = lane / C, cc = lane - (lane / C) * C;
     auto advance = [&](int &r_, int &c_) {
@@ -387,7 +253,7 @@ __device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int
         int r1 = rr, c1 = cc;
         advance(r1, c1);
         const bool act1 = base + kWarp + lane < E;
-        const int a0 = L[p0 + rr * NT] * ld, a1 = act1 ? L[p0 + r1 * NT] * ld : 0;
+        const int a0 = row_of(p0 + rr * NT) * ld, a1 = act1 ? row_of(p0 + r1 * NT) * ld : 0;
         const double l0 = A[a0 + k], u0 = A[prow * ld + j0 + cc], v0 = A[a0 + j0 + cc];
         double l1 = 0.0, u1 = 0.0, v1 = 0.0;
         if (act1) {
@@ -402,7 +268,7 @@ __device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int
         advance(rr, cc);
     }
     if (base < E && base + lane < E) {
-        const int a0 = L[p0 + rr * NT] * ld;
+        const int a0 = row_of(p0 + rr * NT) * ld;
         A[a0 + j0 + cc] = fma(-A[a0 + k], A[prow * ld + j0 + cc], A[a0 + j0 + cc]);
     }
 }
@@ -534,7 +400,7 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
                 pivot_step(A, ld, m, k + 1, L, Ln, invp, flag, lane);
             }
             if (warp > 0 && k + 2 <= m)  // rows at positions k + 1 + (warp - 1), step NT
-                trailing_update_flat(A, ld, m, k, k + 2, L, k + warp, NT, lane);
+                trailing_update_flat<true>(A, ld, m, k, k + 2, L, k + warp, NT, lane);
             __syncthreads();
             if (*flag) return RBFSL_ESINGULAR;
             if (k + 1 < m) {
@@ -595,15 +461,8 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
         }
         gsync();
         if (*flag) return RBFSL_ESINGULAR;
-        // trailing update: rows k+1.. cyclic over the NW warps, lanes over the m - k columns
-        // k+1..m in chunks of 32 (pivot row in registers)
-        switch ((m - k + kWarp - 1) / kWarp) {
-            case 1: trailing_update<NW, 1>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 2: trailing_update<NW, 2>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 3: trailing_update<NW, 3>(A, ld, m, k, k + 1 + warp, lane); break;
-            case 4: trailing_update<NW, 4>(A, ld, m, k, k + 1 + warp, lane); break;
-            default: trailing_update<NW, 5>(A, ld, m, k, k + 1 + warp, lane); break;
-        }
+        // trailing update: rows k+1.. cyclic over the NW warps, columns k+1..m, flattened
+        trailing_update_flat<false>(A, ld, m, k, k + 1, nullptr, k + 1 + warp, NW, lane);
         gsync();
     }
     if (warp != 0) return RBFSL_OK;
