@@ -224,51 +224,63 @@ __host__ __device__ inline int knn_cap(int k) {
     while (cap < 3 * k) cap <<= 1;
     return cap;
 }
-// Trailing update of step k, flattened: the warp's rows (list positions p0, p0 + NT, ... < m)
-// times the columns j0..m form one index space that the 32 lanes walk in consecutive chunks,
-// so that only the last chunk of the step has idle lanes (a per-row chunking leaves the last
-// chunk of every row partly idle, and an idle lane of a DFMA still costs FP64 pipe time). Per
-// element the multiplier, the pivot-row value and the element are loaded from shared memory;
-// two chunks are loaded before either is stored. Same FMA per element as trailing_update.
-// With kList false the rows are in place (position = row, pivot row k), L unused.
-template <bool kList>
+// Trailing update of step k, flattened: rows times the columns j0..m form one index space that
+// the lanes walk in 32-element chunks, so that only a step's last chunk has idle lanes (an idle
+// lane of a DFMA still costs FP64 pipe time). kInterleave: the space is all remaining rows (list
+// positions k+1..m-1) and the NT warps take its chunks in turn (warp wi: chunks wi, wi + NT, ...;
+// shares equal to a chunk); otherwise warp wi's space is its own rows, positions k+1+wi, step NT
+// (shares equal to a row; measured better where a pivot warp shares an SM sub-partition with two
+// of the update warps). Per element the multiplier, the pivot-row value and the element are
+// loaded from shared memory; two chunks are loaded before either is stored. One FMA per element:
+// A[r][j] -= A[r][k] * A[pivot][j]. With kList false the rows are in place (position = row,
+// pivot row k) and L is unused.
+template <bool kList, bool kInterleave>
 __device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int ld, int m, int k, int j0,
-                                                     const int *__restrict__ L, int p0, int NT, int lane) {
-    if (p0 >= m) return;
-    const int C = m - j0 + 1;
-    const int R = (m - 1 - p0) / NT + 1;
+                                                     const int *__restrict__ L, int wi, int NT, int lane) {
+    const int first = kInterleave ? k + 1 : k + 1 + wi, step = kInterleave ? 1 : NT;
+    if (first >= m) return;
+    const int R = (m - 1 - first) / step + 1, C = m - j0 + 1;
     const int E = R * C;
+    const int stride = kInterleave ? kWarp * NT : kWarp;
+    int e = (kInterleave ? kWarp * wi : 0) + lane;
+    if (e - lane >= E) return;
     const int prow = kList ? L[k] : k;
-    auto row_of = [&](int pos) { return kList ? L[pos] : pos; };
-    const int q = kWarp / C, rem = kWarp - q * C;  // a step of 32 elements: q rows and rem columns
-    int rr = lane / C, cc = lane - (lane / C) * C;
+    auto row_of = [&](int rr) {
+        const int pos = first + rr * step;
+        return kList ? L[pos] : pos;
+    };
+    const int q = stride / C, rem = stride - q * C;  // one chunk turn: q rows and rem columns
+    int rr = e / C, cc = e - (e / C) * C;
     auto advance = [&](int &r_, int &c_) {
         r_ += q;
         c_ += rem;
         if (c_ >= C) { c_ -= C; ++r_; }
     };
-    int base = 0;
-    for (; base + kWarp < E; base += 2 * kWarp) {
-        // chunk base (all lanes active) and chunk base + 32 (lanes below E)
+    for (; e - lane + stride < E; e += 2 * stride) {
+        // chunk e - lane (all lanes active) and the next one of this warp (lanes below E)
         int r1 = rr, c1 = cc;
         advance(r1, c1);
-        const bool act1 = base + kWarp + lane < E;
-        const int a0 = row_of(p0 + rr * NT) * ld, a1 = act1 ? row_of(p0 + r1 * NT) * ld : 0;
-        const double l0 = A[a0 + k], u0 = A[prow * ld + j0 + cc], v0 = A[a0 + j0 + cc];
-        double l1 = 0.0, u1 = 0.0, v1 = 0.0;
+        const bool act0 = e < E, act1 = e + stride < E;
+        const int a0 = act0 ? row_of(rr) * ld : 0, a1 = act1 ? row_of(r1) * ld : 0;
+        double l0 = 0.0, u0 = 0.0, v0 = 0.0, l1 = 0.0, u1 = 0.0, v1 = 0.0;
+        if (act0) {
+            l0 = A[a0 + k];
+            u0 = A[prow * ld + j0 + cc];
+            v0 = A[a0 + j0 + cc];
+        }
         if (act1) {
             l1 = A[a1 + k];
             u1 = A[prow * ld + j0 + c1];
             v1 = A[a1 + j0 + c1];
         }
-        A[a0 + j0 + cc] = fma(-l0, u0, v0);
+        if (act0) A[a0 + j0 + cc] = fma(-l0, u0, v0);
         if (act1) A[a1 + j0 + c1] = fma(-l1, u1, v1);
         rr = r1;
         cc = c1;
         advance(rr, cc);
     }
-    if (base < E && base + lane < E) {
-        const int a0 = row_of(p0 + rr * NT) * ld;
+    if (e - lane < E && e < E) {
+        const int a0 = row_of(rr) * ld;
         A[a0 + j0 + cc] = fma(-A[a0 + k], A[prow * ld + j0 + cc], A[a0 + j0 + cc]);
     }
 }
@@ -399,8 +411,7 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
                 __syncwarp();
                 pivot_step(A, ld, m, k + 1, L, Ln, invp, flag, lane);
             }
-            if (warp > 0 && k + 2 <= m)  // rows at positions k + 1 + (warp - 1), step NT
-                trailing_update_flat<true>(A, ld, m, k, k + 2, L, k + warp, NT, lane);
+            if (warp > 0 && k + 2 <= m) trailing_update_flat<true, false>(A, ld, m, k, k + 2, L, warp - 1, NT, lane);
             __syncthreads();
             if (*flag) return RBFSL_ESINGULAR;
             if (k + 1 < m) {
@@ -461,8 +472,8 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
         }
         gsync();
         if (*flag) return RBFSL_ESINGULAR;
-        // trailing update: rows k+1.. cyclic over the NW warps, columns k+1..m, flattened
-        trailing_update_flat<false>(A, ld, m, k, k + 1, nullptr, k + 1 + warp, NW, lane);
+        // trailing update: rows k+1..m-1, columns k+1..m, flattened over the NW warps
+        trailing_update_flat<false, true>(A, ld, m, k, k + 1, nullptr, warp, NW, lane);
         gsync();
     }
     if (warp != 0) return RBFSL_OK;
