@@ -197,6 +197,39 @@ int launch_gemm_sub(const double *A, int64_t lda, const double *B, int64_t ldb, 
     return launch_status("gemm_sub_f64");
 }
 
+// The solve's trailing update C[M x T] -= A[M x K] B[K x T] (K <= 64, row-major), one warp per
+// row of C: lanes over columns (two per lane per 64-column pass), the row's K factor entries held
+// by the lanes and broadcast by shuffles, B read through L1. Small-grid GEMM tiles would give a
+// block step only about one warp per SM sub-partition; rows per warp keep the rounds balanced.
+// Same accumulation order per element as gemm_sub_f64 (k ascending, then subtracted).
+__global__ void __launch_bounds__(256) gemm_rows_sub(const double *__restrict__ Am, int64_t lda,
+                                                     const double *__restrict__ Bm, int64_t ldb,
+                                                     double *__restrict__ Cm, int64_t ldc, int64_t M, int T, int K) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= M) return;
+    const double a_lo = lane < K ? Am[row * lda + lane] : 0.0;
+    const double a_hi = lane + kWarp < K ? Am[row * lda + lane + kWarp] : 0.0;
+    for (int c0 = 0; c0 < T; c0 += 2 * kWarp) {
+        const int c1 = c0 + lane, c2 = c0 + kWarp + lane;
+        double acc1 = 0.0, acc2 = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double a = __shfl_sync(0xffffffffu, k < kWarp ? a_lo : a_hi, k & (kWarp - 1));
+            if (c1 < T) acc1 = fma(a, Bm[k * ldb + c1], acc1);
+            if (c2 < T) acc2 = fma(a, Bm[k * ldb + c2], acc2);
+        }
+        if (c1 < T) Cm[row * ldc + c1] -= acc1;
+        if (c2 < T) Cm[row * ldc + c2] -= acc2;
+    }
+}
+
+int launch_gemm_rows_sub(const double *A, int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                         int64_t M, int T, int K, cudaStream_t s) {
+    if (M <= 0 || T <= 0 || K <= 0) return RBFSL_OK;
+    gemm_rows_sub<<<(unsigned)((M * kWarp + 255) / 256), 256, 0, s>>>(A, lda, B, ldb, C, ldc, M, T, K);
+    return launch_status("gemm_rows_sub");
+}
+
 int global_factor(double *A, int64_t N, int32_t *piv, int32_t *status, cudaStream_t s) {
     for (int64_t j0 = 0; j0 < N; j0 += kNb) {
         const int nb = (int)std::min<int64_t>(kNb, N - j0);
@@ -230,71 +263,82 @@ __global__ void gather_rows(const double *__restrict__ Q, const int32_t *__restr
     Y[e] = Q[(int64_t)perm[i] * T + (e - i * T)];
 }
 
-// In-place solve of the diagonal block (rows r0..r0+nb) for a tile of 64 right-hand sides:
-// unit lower (forward) or upper with stored diagonal (backward). Column-oriented
-// substitution: after row r is final, all threads update the remaining rows in parallel.
-__global__ void __launch_bounds__(256) trsm_diag_block(const double *__restrict__ LU, int64_t N,
-                                                       int64_t r0, int nb, double *__restrict__ Y,
-                                                       int T, int upper) {
-    extern __shared__ double sm[];
-    double *D = sm;                      // nb x (kNb + 1)
-    double *Ys = sm + kNb * (kNb + 1);   // nb x 64
-    const int t = threadIdx.x;
-    const int c0 = blockIdx.x * 64;
-    const int tw = min(64, T - c0);
-    for (int e = t; e < nb * nb; e += blockDim.x) D[(e / nb) * (kNb + 1) + e % nb] = LU[(r0 + e / nb) * N + r0 + e % nb];
-    for (int e = t; e < nb * 64; e += blockDim.x) {
-        const int r = e / 64, c = e % 64;
-        Ys[e] = c < tw ? Y[(r0 + r) * T + c0 + c] : 0.0;
+// In-place solve of the diagonal block (rows r0..r0+nb) of the factor: unit lower (forward) or
+// upper with stored diagonal (backward), column-oriented substitution, one warp per right-hand
+// side, kTrsmCols warps (right-hand sides) per block. A 64 x 64 triangular solve with T
+// right-hand sides is T * 64^2 / 2 FP64 FMAs, too many for one SM's FP64 rate, so the columns go
+// to different SMs. The block's warps stage the diagonal block in shared memory together (eight
+// loads in flight per thread), then lane l of each warp holds rows l and l + 32 in registers and
+// each step broadcasts the finished value by a shuffle.
+constexpr int kTrsmCols = 4;
+
+__global__ void __launch_bounds__(kTrsmCols * 32) trsm_diag_col(const double *__restrict__ LU, int64_t N, int64_t r0,
+                                                                int nb, double *__restrict__ Y, int T, int upper) {
+    __shared__ double D[kNb][kNb + 1];
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kTrsmCols + (threadIdx.x >> 5);
+    const int nn = nb * nb;
+    for (int e0 = threadIdx.x; e0 < nn; e0 += 8 * kTrsmCols * kWarp) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * kTrsmCols * kWarp;
+            v[u] = e < nn ? LU[(r0 + e / nb) * N + r0 + e % nb] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * kTrsmCols * kWarp;
+            if (e < nn) D[e / nb][e % nb] = v[u];
+        }
     }
     __syncthreads();
+    if (c >= T) return;
+    double y0 = lane < nb ? Y[(r0 + lane) * T + c] : 0.0;
+    double y1 = lane + kWarp < nb ? Y[(r0 + lane + kWarp) * T + c] : 0.0;
+    const int s0 = lane, s1 = lane + kWarp;
     if (!upper) {
         for (int r = 0; r < nb - 1; ++r) {
-            const int rows = nb - 1 - r;
-            for (int e = t; e < rows * 64; e += blockDim.x) {
-                const int s = r + 1 + e / 64, c = e % 64;
-                Ys[s * 64 + c] = fma(-D[s * (kNb + 1) + r], Ys[r * 64 + c], Ys[s * 64 + c]);
-            }
-            __syncthreads();
+            const double yr = __shfl_sync(0xffffffffu, r < kWarp ? y0 : y1, r & (kWarp - 1));
+            if (r < kWarp && s0 > r && s0 < nb) y0 = fma(-D[s0][r], yr, y0);  // rows < 32 done after r = 31
+            if (s1 > r && s1 < nb) y1 = fma(-D[s1][r], yr, y1);
         }
     } else {
+        // reciprocal pivots, all at once, so that a step's multiply replaces a division
+        const double i0 = lane < nb ? 1.0 / D[lane][lane] : 0.0;
+        const double i1 = lane + kWarp < nb ? 1.0 / D[lane + kWarp][lane + kWarp] : 0.0;
         for (int r = nb - 1; r >= 0; --r) {
-            if (t < 64) Ys[r * 64 + t] /= D[r * (kNb + 1) + r];
-            __syncthreads();
-            for (int e = t; e < r * 64; e += blockDim.x) {
-                const int s = e / 64, c = e % 64;
-                Ys[s * 64 + c] = fma(-D[s * (kNb + 1) + r], Ys[r * 64 + c], Ys[s * 64 + c]);
+            if (r < kWarp) {
+                if (lane == r) y0 *= i0;
+            } else if (lane == r - kWarp) {
+                y1 *= i1;
             }
-            __syncthreads();
+            const double yr = __shfl_sync(0xffffffffu, r < kWarp ? y0 : y1, r & (kWarp - 1));
+            if (s0 < r) y0 = fma(-D[s0][r], yr, y0);
+            if (r > kWarp && s1 < r) y1 = fma(-D[s1][r], yr, y1);  // rows >= 32 done below r = 33
         }
     }
-    for (int e = t; e < nb * 64; e += blockDim.x) {
-        const int r = e / 64, c = e % 64;
-        if (c < tw) Y[(r0 + r) * T + c0 + c] = Ys[e];
-    }
+    if (lane < nb) Y[(r0 + lane) * T + c] = y0;
+    if (lane + kWarp < nb) Y[(r0 + lane + kWarp) * T + c] = y1;
 }
 
 int global_solve(const double *LU, const int32_t *perm, int64_t N, const double *Q, int T,
                  double *C, cudaStream_t s) {
     const int64_t NT = N * T;
     gather_rows<<<(unsigned)((NT + 255) / 256), 256, 0, s>>>(Q, perm, N, T, C);
-    const unsigned tb = (unsigned)((T + 63) / 64);
-    const int smem = (kNb * (kNb + 1) + kNb * 64) * (int)sizeof(double);
-    RBFSL_CUDA_TRY(cudaFuncSetAttribute(trsm_diag_block, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     // forward: L y = P q
     for (int64_t r0 = 0; r0 < N; r0 += kNb) {
         const int nb = (int)std::min<int64_t>(kNb, N - r0);
-        trsm_diag_block<<<tb, 256, smem, s>>>(LU, N, r0, nb, C, T, 0);
-        int rc = launch_gemm_sub(LU + (r0 + nb) * N + r0, N, C + r0 * T, T, C + (r0 + nb) * T, T,
-                                 N - r0 - nb, T, nb, s);
+        trsm_diag_col<<<(unsigned)((T + kTrsmCols - 1) / kTrsmCols), kTrsmCols * 32, 0, s>>>(LU, N, r0, nb, C, T, 0);
+        int rc = launch_gemm_rows_sub(LU + (r0 + nb) * N + r0, N, C + r0 * T, T, C + (r0 + nb) * T, T,
+                                      N - r0 - nb, T, nb, s);
         if (rc) return rc;
     }
     // backward: U c = y
     const int64_t last = ((N - 1) / kNb) * kNb;
     for (int64_t r0 = last; r0 >= 0; r0 -= kNb) {
         const int nb = (int)std::min<int64_t>(kNb, N - r0);
-        trsm_diag_block<<<tb, 256, smem, s>>>(LU, N, r0, nb, C, T, 1);
-        int rc = launch_gemm_sub(LU + r0, N, C + r0 * T, T, C, T, r0, T, nb, s);
+        trsm_diag_col<<<(unsigned)((T + kTrsmCols - 1) / kTrsmCols), kTrsmCols * 32, 0, s>>>(LU, N, r0, nb, C, T, 1);
+        int rc = launch_gemm_rows_sub(LU + r0, N, C + r0 * T, T, C, T, r0, T, nb, s);
         if (rc) return rc;
     }
     return launch_status("global_solve");
