@@ -97,6 +97,38 @@ __device__ __forceinline__ void sh_eval(int ell, double x, double y, double z, O
     }
 }
 
+// sh_eval spread over a warp, one lane per order m (lanes 0..ell; the others return at once):
+// lane m forms (x + iy)^m by sh_eval's recurrence and then the degrees l = m..ell, so every
+// value comes from the same operations as in sh_eval while the serial chain is one order long.
+template <typename Out>
+__device__ __forceinline__ void sh_eval_lanes(int ell, double x, double y, double z, int lane, Out out) {
+    if (lane > ell) return;
+    const int m = lane;
+    double cm = 1.0, sm = 0.0;
+    for (int mm = 1; mm <= m; ++mm) {
+        const double c2 = cm * x - sm * y;
+        const double s2 = cm * y + sm * x;
+        cm = c2;
+        sm = s2;
+    }
+    double q2 = 0.0, q1 = 0.0;
+    for (int l = m; l <= ell; ++l) {
+        const int id = l * l + l + m;
+        double q;
+        if (l == m) q = c_sh.qmm[m];
+        else q = c_sh.a[id] * z * q1 - c_sh.b[id] * q2;
+        const double kq = c_sh.K[id] * q;
+        if (m == 0) {
+            out(id, kq);
+        } else {
+            out(id, kq * cm);
+            out(l * l + l - m, kq * sm);
+        }
+        q2 = q1;
+        q1 = q;
+    }
+}
+
 // Polyharmonic spline r^p (p odd) from the squared distance: r * (r^2)^((p-1)/2).
 __device__ __forceinline__ double phs_from_d2(double d2, int half) {
     double v = sqrt(d2);

@@ -378,7 +378,7 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
         A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
     }
     for (int e = t; e < M * M; e += GT) A[(n + e / M) * ld + n + e % M] = 0.0;
-    if (t == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { A[(n + c) * ld + m] = v; });
+    if (warp == 0) sh_eval_lanes(ell, px, py, pz, lane, [&](int c, double v) { A[(n + c) * ld + m] = v; });
     gsync();
 
     if constexpr (NW > 1 && NW % 4 == 1) {
@@ -491,8 +491,8 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
 
 // Centre-stencil weights of one point by one warp (Sec. 3.3): the point uses the stencil
 // S = Ik[k] of its nearest node k, whose m x m saddle-point matrix was factorised once. Ft is
-// that factor stored column-major with its diagonal replaced by the reciprocal (Ft[c m + r] =
-// L_rc or U_rc, Ft[c m + c] = 1 / U_cc), pr its row order. b = [phi(|p - x_Sj|); Y(p)], then
+// that factor stored column-major, the upper columns scaled by the reciprocal diagonal
+// (Ft[c m + r] = L_rc below the diagonal, U_rc / U_cc above it, 1 / U_cc on it), pr its row order. b = [phi(|p - x_Sj|); Y(p)], then
 // L U w~ = P b by column-oriented substitution: lane l keeps rows l, l+32, ... of the
 // right-hand side in registers; after row c is final it is broadcast by a shuffle and every lane
 // updates its later (earlier) rows with one coalesced column of the factor. b: m shared
@@ -507,7 +507,7 @@ __device__ __forceinline__ void center_point_nu(const double *__restrict__ X, co
         const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
         b[j] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
     }
-    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { b[n + c] = v; });
+    sh_eval_lanes(ell, px, py, pz, lane, [&](int c, double v) { b[n + c] = v; });
     __syncwarp();
     double y[NU];
 #pragma unroll
@@ -553,28 +553,37 @@ __device__ __forceinline__ void center_point_nu(const double *__restrict__ X, co
 #pragma unroll
         for (int u = 0; u < NU; ++u) { c0[u] = c1[u]; c1[u] = c2[u]; }
     }
-    // backward: upper, reciprocal diagonal (the diagonal entry of column c is its row c)
+    // backward: upper with columns pre-scaled by the reciprocal diagonal (Ft[c m + r] = U_rc / U_cc
+    // above the diagonal, 1 / U_cc on it): y_r -= Ft[c m + r] y_c for r < c, and at the end
+    // x_r = y_r / U_rr, one multiply per row (kept aside as row r's diagonal entry passes by)
+    double dg[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) dg[u] = 0.0;
     load_upper(m - 1, c0);
     load_upper(m - 2, c1);
     for (int c = m - 1; c >= 0; --c) {
         load_upper(c - 2, c2);
         const int uc = c >> 5;
-        double own = 0.0, dinv = 0.0;
+        double own = 0.0;
 #pragma unroll
         for (int u = 0; u < NU; ++u)
-            if (u == uc) { own = y[u]; dinv = c0[u]; }
-        const double xc = __shfl_sync(0xffffffffu, own, c & 31) * __shfl_sync(0xffffffffu, dinv, c & 31);
+            if (u == uc) {
+                own = y[u];
+                if (lane == (c & 31)) dg[u] = c0[u];
+            }
+        const double yc = __shfl_sync(0xffffffffu, own, c & 31);
 #pragma unroll
         for (int u = 0; u < NU; ++u) {
-            if (u == uc && lane == (c & 31)) y[u] = xc;
             if (u <= ((c - 1) >> 5) && c > 0) {
                 const int r = lane + 32 * u;
-                if (r < c) y[u] = fma(-c0[u], xc, y[u]);
+                if (r < c) y[u] = fma(-c0[u], yc, y[u]);
             }
         }
 #pragma unroll
         for (int u = 0; u < NU; ++u) { c0[u] = c1[u]; c1[u] = c2[u]; }
     }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) y[u] *= dg[u];
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
         const int r = lane + 32 * u;

@@ -167,10 +167,12 @@ __global__ void __launch_bounds__(128) pu_factor_kernel(const double *__restrict
     double *out = LU + lu_off[l];
     if (!colmajor) {
         for (int e = t; e < m * m; e += 128) out[e] = A[(e / m) * ld + e % m];
-    } else {  // column-major, diagonal replaced by its reciprocal (centre stencils)
+    } else {  // column-major, upper columns scaled by the reciprocal diagonal, which is stored on
+              // the diagonal (centre stencils: the backward substitution multiplies once per row)
         for (int e = t; e < m * m; e += 128) {
             const int c = e / m, r = e % m;
-            out[e] = r == c ? 1.0 / A[r * ld + c] : A[r * ld + c];
+            const double inv = 1.0 / A[c * ld + c];
+            out[e] = r == c ? inv : (r < c ? A[r * ld + c] * inv : A[r * ld + c]);
         }
     }
     int32_t *pr = perm + mstart[l] + l * M;
