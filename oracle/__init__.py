@@ -65,6 +65,7 @@ def lib():
                 "orc_num_threads": (_I, []),
                 "orc_velocity": (None, [_I, _P, _P, _D, _P]),
                 "orc_trace_rk4": (None, [_I, _P, _P, _I64, _D, _D, _P]),
+                "orc_trace_rk5": (None, [_I, _P, _P, _I64, _D, _D, _P]),
                 "orc_knn": (None, [_P, _I64, _P, _I64, _I, _P, _P]),
                 "orc_sh_eval": (None, [_I, _P, _P]),
                 "orc_gepp_solve": (_I, [_P, _I, _P, _I]),
@@ -117,6 +118,14 @@ def trace_rk4(X, kind, prm, t1, dt):
     """Departure points of every node for the step (t1 - dt, t1] (Eq. sl_ode, RK4)."""
     X = _f64(X); prm = _f64(prm); Xi = np.empty_like(X)
     lib().orc_trace_rk4(kind, _ptr(prm), _ptr(X), X.shape[0], t1, dt, _ptr(Xi))
+    return Xi
+
+
+def trace_rk5(X, kind, prm, t1, dt):
+    """Departure points of every node for the step (t1 - dt, t1] (Eq. sl_ode, Fehlberg's
+    fifth-order formula, every stage projected)."""
+    X = _f64(X); prm = _f64(prm); Xi = np.empty_like(X)
+    lib().orc_trace_rk5(kind, _ptr(prm), _ptr(X), X.shape[0], t1, dt, _ptr(Xi))
     return Xi
 
 

@@ -88,6 +88,46 @@ void orc_trace_rk4(int kind, const double *prm, const double *X, int64_t N, doub
     }
 }
 
+/* The same step with Fehlberg's fifth-order Runge-Kutta formula (the paper's final integrator
+ * choice, Sec. 3.2): six stages, nodes c = (0, 1/4, 3/8, 12/13, 1, 1/2), the published
+ * coupling coefficients a_ij and the fifth-order weights b = (16/135, 0, 6656/12825,
+ * 28561/56430, -9/50, 2/55). Stage point i is x + h sum_j a_ij k_j, projected onto S^2 before
+ * u is evaluated there at t1 + c_i h; the result x + h sum_i b_i k_i is projected too. */
+void orc_trace_rk5(int kind, const double *prm, const double *X, int64_t N, double t1,
+                   double dt, double *Xi) {
+    static const double c[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+    static const double a[6][5] = {
+        {0, 0, 0, 0, 0},
+        {1.0 / 4.0, 0, 0, 0, 0},
+        {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+        {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+        {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+        {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+    static const double b[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+    const double h = -dt;
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < N; ++j) {
+        const double *x = X + 3 * j;
+        double k[6][3], y[3];
+        for (int i = 0; i < 6; ++i) {
+            for (int d = 0; d < 3; ++d) {
+                double s = 0.0;
+                for (int q = 0; q < i; ++q) s += a[i][q] * k[q][d];
+                y[d] = x[d] + h * s;
+            }
+            if (i > 0) project(y);
+            orc_velocity(kind, prm, y, t1 + c[i] * h, k[i]);
+        }
+        double *xi = Xi + 3 * j;
+        for (int d = 0; d < 3; ++d) {
+            double s = 0.0;
+            for (int i = 0; i < 6; ++i) s += b[i] * k[i][d];
+            xi[d] = x[d] + h * s;
+        }
+        project(xi);
+    }
+}
+
 /* ------------------------------------------------------------------ brute-force k-NN */
 /* The kd-tree of Sec. 3.3 returns the k nearest nodes; here every node is tested.
  * Key (d2, j) with d2 = ((qx-xx)^2 + (qy-xy)^2) + (qz-xz)^2, each operation rounded.

@@ -94,3 +94,36 @@ def test_tracer_returns_after_one_period(orc, kind):
         P = orc.trace_rk4(P, kind, prm, m * dt, dt)
     bound = 5e-7 if kind == 0 else 1e-5
     assert np.abs(P - X).max() < bound
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_rk5_matches_closed_form_with_sixth_order_local_error(orc, kind):
+    """Fehlberg's fifth-order formula (Sec. 3.2): local error O(dt^6) against the closed-form
+    flow maps (halving dt divides it by ~64), and well below the RK4 step's error. A wrong
+    tableau entry breaks the order."""
+    prm = _rigid() if kind == 0 else _deform()
+    X = inputs.nodes(2562, 5)
+    errs = []
+    for S in (30, 60, 120):
+        dt = 1.0 / S
+        t1 = 0.2 + dt
+        ex = orc.exact_departure(X, kind, prm, t1 - dt, t1)
+        Xi = orc.trace_rk5(X, kind, prm, t1, dt)
+        errs.append(np.abs(Xi - ex).max())
+        assert errs[-1] < np.abs(orc.trace_rk4(X, kind, prm, t1, dt) - ex).max() / 10
+        np.testing.assert_allclose(np.linalg.norm(Xi, axis=1), 1.0, atol=2e-16 * 4)
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 45 < r1 < 85 and 45 < r2 < 85, errs
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_rk5_tracer_returns_after_one_period(orc, kind):
+    prm = _rigid() if kind == 0 else _deform()
+    X = inputs.nodes(500, 9)
+    S = 120
+    dt = 1.0 / S
+    P = X.copy()
+    for m in range(S, 0, -1):
+        P = orc.trace_rk5(P, kind, prm, m * dt, dt)
+    bound = 1e-8 if kind == 0 else 1e-7
+    assert np.abs(P - X).max() < bound
