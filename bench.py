@@ -663,6 +663,20 @@ def main():
                         "p50_ms": float(np.percentile(cms, 50)), "p99_ms": float(np.percentile(cms, 99)),
                         "setup_s": setup_s}
 
+    # the paper's final integrator (Fehlberg, fifth order) against RK4 at four times the step:
+    # centre stencils, mixed precision, the deformation run in 150 steps; error vs exact
+    integ = {}
+    if args.accuracy_steps > 0:
+        from paper_1804_01609_gb300 import inputs as _inp
+        w4 = _inp.config_local_deformation(steps=150)
+        for order in (rbfsl.RK4, rbfsl.RK5):
+            c4 = make_ctx(w4, rbfsl.MIXED, stream, rbfsl, mode=rbfsl.CENTER)
+            c4.set_integrator(order)
+            c4.step(w4.steps)
+            integ[f"rk{order}_l2_vs_exact"] = rel_l2(c4.get_q(), w4.q0())
+            c4.close()
+        integ["steps"] = 150
+
     # ---- end to end through the public API with host buffers (pinned), per step:
     # H2D of the field, one SL step, D2H of the new field
     ctx = make_ctx(w, rbfsl.MIXED, stream, rbfsl)
@@ -736,6 +750,7 @@ def main():
                             "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
         "center_stencils": center,
+        "integrator_at_dt_1_150": integ,
         "global_N10242_T64": glob,
         "batched_64_problems": batched,
         "served": served,

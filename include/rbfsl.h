@@ -87,10 +87,19 @@ enum { RBFSL_HOST = 0, RBFSL_DEVICE = 1 }; /* where a caller buffer lives */
  * backward from (x_j, t1) to t1 - dt with classical RK4 (h = -dt), projecting every stage
  * point and the result orthogonally onto S^2.
  *   x, xi: device, N x 3 doubles (may not alias). vel_params: HOST array (4 or 2 doubles).
- *   precision RBFSL_FP64 traces in FP64; RBFSL_MIXED evaluates the stages in FP32 and adds
- *   the FP32 displacement to the FP64 node before the final FP64 projection.
+ *   precision RBFSL_FP64 traces in FP64; RBFSL_MIXED computes the node's own velocity, the
+ *   time factors and the final add and projection in FP64 and the stages as FP32 increments
+ *   from the node (stage offset and velocity change), so FP32 rounding scales with |u| dt.
  * Errors: EINVAL (N < 0, null pointers, unknown kind or precision), ECUDA. */
 int rbfsl_trace_rk4(const double *x, int64_t N, int vel_kind, const double *vel_params,
+                    double t1, double dt, int precision, double *xi, void *stream);
+
+/* The same departure points with Fehlberg's fifth-order Runge-Kutta formula, the paper's final
+ * integrator choice (Sec. 3.2): six stages (nodes 0, 1/4, 3/8, 12/13, 1, 1/2 and the published
+ * coupling coefficients), fifth-order weights 16/135, 0, 6656/12825, 28561/56430, -9/50, 2/55;
+ * every stage point and the result projected onto S^2. Arguments, precisions and errors as
+ * rbfsl_trace_rk4. */
+int rbfsl_trace_rk5(const double *x, int64_t N, int vel_kind, const double *vel_params,
                     double t1, double dt, int precision, double *xi, void *stream);
 
 /* Spatial index for k-nearest-neighbour queries over a fixed node set (replaces the
@@ -265,6 +274,11 @@ int rbfsl_set_pu(rbfsl_ctx *ctx, const double *centers, int64_t Mp, double radiu
                  int weight_kind, int mem);
 int rbfsl_set_precision(rbfsl_ctx *ctx, int precision);
 int rbfsl_set_dt(rbfsl_ctx *ctx, double dt);
+/* Departure-point integrator of the context's steps (Sec. 3.2): RBFSL_RK4 (default) or RBFSL_RK5
+ * (Fehlberg's fifth-order formula, as rbfsl_trace_rk5). Takes effect at the next step; the
+ * batched and served paths trace with RK4. Errors: EINVAL. */
+enum { RBFSL_RK4 = 4, RBFSL_RK5 = 5 };
+int rbfsl_set_integrator(rbfsl_ctx *ctx, int order);
 int rbfsl_set_time(rbfsl_ctx *ctx, double t);
 /* Initial field q(X, t): N x T, element type dtype (converted to the context precision),
  * on the host (copied synchronously) or the device (copied on the context stream).

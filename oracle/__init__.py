@@ -225,12 +225,14 @@ def local_apply(X, Xi, q, n, L, kkind, kprm, mode=DIRECT, want_IW=False):
     return (out, I, W) if want_IW else out
 
 
-def local_run(X, q0, n, L, power, vel_kind, vel_prm, dt, steps, mode=DIRECT, t0=0.0):
-    """Algorithm 1 with the local method: `steps` steps of size dt from t0."""
+def local_run(X, q0, n, L, power, vel_kind, vel_prm, dt, steps, mode=DIRECT, t0=0.0, integrator=4):
+    """Algorithm 1 with the local method: `steps` steps of size dt from t0, departure points
+    by RK4 (integrator 4) or Fehlberg's fifth-order formula (integrator 5)."""
     q = _f64(q0)
+    trace = trace_rk5 if integrator == 5 else trace_rk4
     for m in range(steps):
         t1 = t0 + (m + 1) * dt
-        Xi = trace_rk4(X, vel_kind, vel_prm, t1, dt)
+        Xi = trace(X, vel_kind, vel_prm, t1, dt)
         q = local_apply(X, Xi, q, n, L, PHS, float(power), mode)
     return q
 

@@ -72,6 +72,7 @@ struct rbfsl_ctx {
     double kparam = 3.0;
     int precision = RBFSL_FP64;
     double dt = 0.0, t = 0.0;
+    int integrator = RBFSL_RK4;
     int T = 0;
     void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 pairs (mixed), 8 bytes each
     int64_t steps_done = 0;
@@ -201,7 +202,7 @@ int one_step_global(rbfsl_ctx *c) {
     const int64_t N = c->N, NT = N * (int64_t)c->T;
     const double t1 = c->t + c->dt;
     const unsigned blocks = (unsigned)((NT + 255) / 256);
-    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->integrator, c->xi, c->stream));
     if (c->precision == RBFSL_FP64) {
         CTX_RC(c, global_solve(c->LU, c->perm, N, (const double *)c->q, c->T, c->C64, c->stream));
         CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T, RBFSL_F64,
@@ -254,7 +255,7 @@ int prepare_pu(rbfsl_ctx *c) {
 int one_step_pu(rbfsl_ctx *c) {
     const int64_t N = c->N, NT = N * (int64_t)c->T;
     const double t1 = c->t + c->dt;
-    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->integrator, c->xi, c->stream));
     const double *q64 = (const double *)c->q;
     const unsigned blocks = (unsigned)((NT + 255) / 256);
     if (c->precision == RBFSL_MIXED) {
@@ -343,7 +344,7 @@ int one_step(rbfsl_ctx *c) {
     const int n = c->n, ell = effective_ell(c), pw = (int)c->kparam;
     const double t1 = c->t + c->dt;
     const int wdt = c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2;
-    CTX_RC(c, launch_trace(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->xi, c->stream));
+    CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->integrator, c->xi, c->stream));
     if (c->mode == RBFSL_DIRECT) {
         CTX_RC(c, launch_knn(c->knn, c->xi, N, n, c->I, c->status, c->stream));
         CTX_RC(c, launch_weights(c->X, c->I, N, n, ell, pw, c->xi, c->W, wdt, c->status, c->stream));
@@ -507,6 +508,13 @@ int rbfsl_set_precision(rbfsl_ctx *c, int precision) {
     c->q = c->q_next = nullptr;  // the field must be set again in the new precision
     c->T = 0;
     c->precision = precision;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_integrator(rbfsl_ctx *c, int order) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (order != RBFSL_RK4 && order != RBFSL_RK5) return fail(c, RBFSL_EINVAL, "integrator must be RBFSL_RK4 or RBFSL_RK5");
+    c->integrator = order;
     return RBFSL_OK;
 }
 

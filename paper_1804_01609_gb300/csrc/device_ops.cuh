@@ -139,6 +139,118 @@ __device__ __forceinline__ void rk4_point_mixed(const Vel<double> &u, double xd,
     normalize3(ox, oy, oz);
 }
 
+// Fehlberg's fifth-order formula (Sec. 3.2, the paper's final integrator): six stages with
+// nodes c, coupling coefficients a (row i: stage i) and fifth-order weights b, as published.
+struct Rk5 {
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int q) {
+        constexpr double v[6][5] = {{0, 0, 0, 0, 0},
+                                    {1.0 / 4.0, 0, 0, 0, 0},
+                                    {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+                                    {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+                                    {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+                                    {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+        return v[i][q];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+        return v[i];
+    }
+};
+
+// One departure point, FP64, Fehlberg's formula backward (h = -dt): stage point i is
+// x + h sum_j a_ij k_j projected onto S^2, evaluated at t1 + c_i h; the result is projected too.
+__device__ __forceinline__ void rk5_point_f64(const Vel<double> &u, double x, double y, double z, double t1,
+                                              double h, double &ox, double &oy, double &oz) {
+    double kx[6], ky[6], kz[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double sx = x, sy = y, sz = z;
+        if (i > 0) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+#pragma unroll
+            for (int q = 0; q < i; ++q) {
+                ax = ax + Rk5::a(i, q) * kx[q];
+                ay = ay + Rk5::a(i, q) * ky[q];
+                az = az + Rk5::a(i, q) * kz[q];
+            }
+            sx = x + h * ax;
+            sy = y + h * ay;
+            sz = z + h * az;
+            normalize3(sx, sy, sz);
+        }
+        u(sx, sy, sz, t1 + Rk5::c(i) * h, kx[i], ky[i], kz[i]);
+    }
+    double dx = 0.0, dy = 0.0, dz = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        dx = dx + Rk5::b(i) * kx[i];
+        dy = dy + Rk5::b(i) * ky[i];
+        dz = dz + Rk5::b(i) * kz[i];
+    }
+    ox = x + h * dx;
+    oy = y + h * dy;
+    oz = z + h * dz;
+    normalize3(ox, oy, oz);
+}
+
+// Mixed, increment form as rk4_point_mixed: k_i = U0 + D_i with the node's velocity U0 in FP64
+// and the stage increments D_i in FP32; since sum_j a_ij = c_i and sum_i b_i = 1, stage i's
+// displacement is c_i h U0 + h sum_j a_ij D_j and the step's is h U0 + h sum_i b_i D_i.
+__device__ __forceinline__ void rk5_point_mixed(const Vel<double> &u, double xd, double yd, double zd,
+                                                double t1, double h, double &ox, double &oy, double &oz) {
+    double U0x, U0y, U0z;
+    u(xd, yd, zd, t1, U0x, U0y, U0z);
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, k2 = 0.f;
+    double c1 = 0.0;
+    if (u.kind == RBFSL_VEL_RIGID) {
+        w0 = (float)(u.p3 * u.p0); w1 = (float)(u.p3 * u.p1); w2 = (float)(u.p3 * u.p2);
+    } else {
+        c1 = cos(u.p1 * t1);
+        k2 = (float)(2.0 * u.p0);
+    }
+    const float x = (float)xd, y = (float)yd, z = (float)zd;
+    const float hf = (float)h;
+    float Dx[6], Dy[6], Dz[6];
+    Dx[0] = Dy[0] = Dz[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int q = 1; q < i; ++q) {
+            sx = sx + (float)Rk5::a(i, q) * Dx[q];
+            sy = sy + (float)Rk5::a(i, q) * Dy[q];
+            sz = sz + (float)Rk5::a(i, q) * Dz[q];
+        }
+        const double ch = Rk5::c(i) * h;
+        const float ax = (float)(ch * U0x) + hf * sx, ay = (float)(ch * U0y) + hf * sy,
+                    az = (float)(ch * U0z) + hf * sz;
+        float ex, ey, ez;
+        stage_offset(x, y, z, ax, ay, az, ex, ey, ez);
+        float cs = 0.f, dc = 0.f;
+        if (u.kind != RBFSL_VEL_RIGID) {
+            const double ci = cos(u.p1 * (t1 + ch));
+            cs = (float)ci;
+            dc = (float)(ci - c1);
+        }
+        vel_increment(u.kind, w0, w1, w2, k2, cs, dc, x, y, z, ex, ey, ez, Dx[i], Dy[i], Dz[i]);
+    }
+    float ix = 0.f, iy = 0.f, iz = 0.f;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+        ix = ix + (float)Rk5::b(i) * Dx[i];
+        iy = iy + (float)Rk5::b(i) * Dy[i];
+        iz = iz + (float)Rk5::b(i) * Dz[i];
+    }
+    ox = xd + (h * U0x + (double)(hf * ix));
+    oy = yd + (h * U0y + (double)(hf * iy));
+    oz = zd + (h * U0z + (double)(hf * iz));
+    normalize3(ox, oy, oz);
+}
+
 // Kernel-ready velocity parameters (deformation: p1 = pi / T_f).
 inline Vel<double> make_vel64(int kind, const double *prm) {
     const double pi = 3.14159265358979323846;

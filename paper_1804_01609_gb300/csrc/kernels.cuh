@@ -84,6 +84,9 @@ int launch_knn(const rbfsl_knn_index *ix, const double *q, int64_t Nq, int k, in
 int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int ell, int power,
                    const double *p, void *w, int w_dtype, int32_t *status, cudaStream_t s);
 
+int launch_trace_order(const double *x, int64_t N, int vel_kind, const double *prm, double t1, double dt,
+                       int precision, int order, double *xi, cudaStream_t s);
+
 int launch_gather(const int32_t *idx, const void *w, int64_t Nq, int n, const void *q, int T,
                   int dtype, void *q_out, cudaStream_t s);
 

@@ -21,6 +21,7 @@ LOCAL, GLOBAL, PU = 0, 1, 2
 DIRECT, CENTER = 0, 1
 PHS, GAUSS, IMQ = 0, 1, 2
 FP64, MIXED = 0, 1
+RK4, RK5 = 4, 5
 F64, F32, F32X2 = 0, 1, 2
 HOST, DEVICE = 0, 1
 PU_WENDLAND, PU_BSPLINE = 0, 1
@@ -55,6 +56,8 @@ SIGNATURES = {
     "rbfsl_version": (ctypes.c_char_p, []),
     "rbfsl_last_error": (ctypes.c_char_p, [_P]),
     "rbfsl_trace_rk4": (_I, [_P, _I64, _I, _P, _D, _D, _I, _P, _P]),
+    "rbfsl_trace_rk5": (_I, [_P, _I64, _I, _P, _D, _D, _I, _P, _P]),
+    "rbfsl_set_integrator": (_I, [_P, _I]),
     "rbfsl_knn_index_create": (_I, [_P, _P, _I64, _I, _P]),
     "rbfsl_knn_index_destroy": (_I, [_P]),
     "rbfsl_knn_query": (_I, [_P, _P, _I64, _I, _P, _P, _P]),
@@ -165,6 +168,12 @@ def _dtype_code(t):
 def rbfsl_trace_rk4(x, vel_kind, vel_params, t1, dt, precision, xi, stream=None):
     prm = np.ascontiguousarray(vel_params, dtype=np.float64)
     _check(load().rbfsl_trace_rk4(_ptr(x), x.shape[0], vel_kind, prm.ctypes.data, t1, dt,
+                                  precision, _ptr(xi), _stream(stream)))
+
+
+def rbfsl_trace_rk5(x, vel_kind, vel_params, t1, dt, precision, xi, stream=None):
+    prm = np.ascontiguousarray(vel_params, dtype=np.float64)
+    _check(load().rbfsl_trace_rk5(_ptr(x), x.shape[0], vel_kind, prm.ctypes.data, t1, dt,
                                   precision, _ptr(xi), _stream(stream)))
 
 
@@ -508,6 +517,9 @@ class Context:
 
     def set_dt(self, dt):
         self._c(load().rbfsl_set_dt(self._h, float(dt)))
+
+    def set_integrator(self, order):
+        self._c(load().rbfsl_set_integrator(self._h, order))
 
     def set_time(self, t):
         self._c(load().rbfsl_set_time(self._h, float(t)))

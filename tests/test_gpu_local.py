@@ -101,6 +101,28 @@ def test_knn_empty_and_bad_k():
         rbfsl.rbfsl_knn_query(ix, _t(X), 101, torch.empty((100, 101), dtype=torch.int32, device=DEV))
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_trace_rk5_parity(orc, kind):
+    """Fehlberg's fifth-order tracer (Sec. 3.2) against the oracle's: FP64 to rounding; mixed
+    (FP32 stage increments) to 1e-10 at dt = 1/600 as the RK4 tracer, and 16 times that at four
+    times the step (the increments' FP32 rounding grows like |grad u| |u| dt^2)."""
+    X = inputs.nodes(40962, 12)
+    prm = (inputs.rigid_rotation_params(inputs.tilted_axis(0.3)) if kind == 0
+           else inputs.deformation_params(2.4, 1.0))
+    x = _t(X)
+    xi = torch.empty_like(x)
+    for dt, bound in ((1.0 / 600, 1e-10), (1.0 / 150, 1.6e-9)):
+        t1 = 0.3
+        ref = orc.trace_rk5(X, kind, prm, t1, dt)
+        rbfsl.rbfsl_trace_rk5(x, kind, prm, t1, dt, rbfsl.FP64, xi)
+        torch.cuda.synchronize()
+        assert np.abs(xi.cpu().numpy() - ref).max() < 1e-14
+        rbfsl.rbfsl_trace_rk5(x, kind, prm, t1, dt, rbfsl.MIXED, xi)
+        got = xi.cpu().numpy()
+        assert np.abs(got - ref).max() < bound
+        np.testing.assert_allclose(np.linalg.norm(got, axis=1), 1.0, atol=1e-15)
+
+
 def perturb_one_ulp(X, seed=0):
     """Every coordinate moved by one ulp in a random direction."""
     s = np.random.default_rng(seed).choice([-1.0, 1.0], size=X.shape)
@@ -251,6 +273,31 @@ def test_cfg1_full_run_matches_oracle(orc, cfg1, mode):
     assert orc.rel_l2(q, ref) < 1e-10
     q0 = cfg1.q0()
     assert orc.rel_l2(q, q0) < 0.1                # returns after one revolution (method error)
+
+
+def test_cfg1_rk5_run_matches_oracle(orc, cfg1):
+    """The rotation workload through the context with the Fehlberg tracer (rbfsl_set_integrator)
+    against the oracle's run with the same tracer; the field returns after one revolution."""
+    w = cfg1
+    ctx = rbfsl.Context(0)
+    ctx.set_nodes(w.X)
+    ctx.set_velocity(w.vel_kind, w.vel_params)
+    ctx.set_method(rbfsl.LOCAL, rbfsl.DIRECT)
+    ctx.set_stencil_size(w.n)
+    ctx.set_sh_degree(w.ell)
+    ctx.set_kernel(rbfsl.PHS, w.power)
+    ctx.set_integrator(rbfsl.RK5)
+    ctx.set_dt(w.dt)
+    ctx.set_tracers(w.q0())
+    ctx.step(w.steps)
+    q = ctx.get_q()
+    with pytest.raises(rbfsl.RbfslError):
+        ctx.set_integrator(3)
+    ctx.close()
+    ref = orc.local_run(w.X, w.q0(), w.n, w.ell, w.power, w.vel_kind, w.vel_params, w.dt, w.steps,
+                        integrator=5)
+    assert orc.rel_l2(q, ref) < 1e-10
+    assert orc.rel_l2(q, w.q0()) < 0.1
 
 
 def test_cfg1_mixed_precision_error(orc, cfg1):
