@@ -16,6 +16,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                      <= ell, w = e_k at a node, agreement with an mpmath 50-digit solve
   local_step         return of a smooth field after a full revolution within method error
   global_*           interpolation at the nodes, LAPACK solve, Cholesky vs numpy
+  global_cardinal    identity at the nodes (cardinal property), E q equal to solve-then-evaluate,
+                     LAPACK solve of the transposed system, smooth fields between the nodes
   pu_*               partition of unity, interpolation at nodes, reproduction of SH <= ell,
                      B-spline / Wendland closed-form values
 """
@@ -77,6 +79,7 @@ def lib():
                 "orc_local_apply": (_I64, [_P, _I64, _I, _I, _I, _D, _I, _P, _I64, _P, _I, _P, _P, _P]),
                 "orc_global_matrix": (None, [_P, _I64, _I, _D, _P]),
                 "orc_global_eval": (None, [_P, _I64, _P, _I64, _I, _D, _P, _I, _P]),
+                "orc_kernel_matrix": (None, [_P, _I64, _P, _I64, _I, _D, _P]),
                 "orc_pu_phi": (_D, [_I, _D]),
                 "orc_pu_eval": (_I64, [_P, _I64, _P, _P, _I64, _D, _P, _P, _P, _P, _I, _I, _D, _I, _I, _P]),
                 "orc_pu_coefficients": (_I64, [_P, _I64, _P, _P, _P, _I, _I, _D, _P, _I, _P]),
@@ -275,6 +278,24 @@ def global_eval(P, X, C, kkind, kprm):
     lib().orc_global_eval(_ptr(P), P.shape[0], _ptr(X), X.shape[0], kkind, kprm, _ptr(C2),
                           C2.shape[1], _ptr(out))
     return out.reshape((P.shape[0],) + C.shape[1:])
+
+
+def kernel_matrix(P, X, kkind, kprm):
+    """Phi(P, X)[i][j] = phi(|p_i - x_j|), the evaluation matrix of Eq. srbfinterp."""
+    P = _f64(P); X = _f64(X)
+    Phi = np.empty((P.shape[0], X.shape[0]))
+    lib().orc_kernel_matrix(_ptr(P), P.shape[0], _ptr(X), X.shape[0], kkind, kprm, _ptr(Phi))
+    return Phi
+
+
+def global_cardinal(P, X, kkind, kprm):
+    """Cardinal (Lagrange) matrix of the global interpolant at the points P (Sec. 2.1): the
+    interpolant of q at p is phi(p, X) c with A_X c = q (Eqs. srbfinterp, rbf_linsys), so the
+    interpolant at all of P is E q with E = Phi(P, X) A_X^-1 (Nq x N) for every field q. Computed
+    from that definition: E^T = A_X^-T Phi(P, X)^T, with the pivoted LU of A_X^T."""
+    A = global_matrix(X, kkind, kprm)
+    LU, piv = lu_factor(A.T)
+    return lu_solve(LU, piv, kernel_matrix(P, X, kkind, kprm).T).T.copy()
 
 
 class GlobalInterpolator:

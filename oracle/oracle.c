@@ -420,6 +420,15 @@ void orc_global_matrix(const double *X, int64_t N, int kkind, double kprm, doubl
             A[i * N + j] = kernel_of_d2(kkind, kprm, sqdist(X + 3 * i, X + 3 * j));
 }
 
+/* Kernel matrix between point and node sets: Phi[i][j] = phi(|p_i - x_j|) (Eq. srbfinterp). */
+void orc_kernel_matrix(const double *P, int64_t Nq, const double *X, int64_t N, int kkind,
+                       double kprm, double *Phi) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < Nq; ++i)
+        for (int64_t j = 0; j < N; ++j)
+            Phi[i * N + j] = kernel_of_d2(kkind, kprm, sqdist(P + 3 * i, X + 3 * j));
+}
+
 /* Evaluate the global interpolant (Eq. srbfinterp) at Nq points:
  * out[i][t] = sum_j phi(|p_i - x_j|) C[j][t], j ascending. */
 void orc_global_eval(const double *P, int64_t Nq, const double *X, int64_t N, int kkind,

@@ -1,7 +1,8 @@
 """Pins for the oracle's global RBF and RBF-PU interpolation (Sec. 2.1, 2.3, 3.3).
 
 Global: the interpolant reproduces the data at the nodes (Eq. rbf_linsys), the evaluation
-equals numpy's dense product, smooth fields are reproduced between the nodes.
+equals numpy's dense product, smooth fields are reproduced between the nodes; the cardinal
+matrix is the identity at the nodes and applies as solve-then-evaluate.
 PU: closed-form values of the weight functions (Eq. bspline, Wendland C2), partition of
 unity (constants reproduced), interpolation at the nodes, exact reproduction of spherical
 harmonics of degree <= ell (each patch interpolant reproduces them, Eq. rbf_poly).
@@ -31,6 +32,28 @@ def test_global_interpolates_at_nodes_and_between(orc):
     s = G.apply(P, f)
     exact = inputs.gaussian_hills(P, [[0.6, 0.8, 0.0]], 5.0, 0.95)
     assert np.abs(s - exact).max() < 5e-4  # a smooth field is well resolved at N = 642
+
+
+@pytest.mark.parametrize("kkind,eps", [(1, 6.0), (2, 4.0)])
+def test_global_cardinal_matrix(orc, kkind, eps):
+    """E = Phi(P, X) A_X^-1 (Sec. 2.1): at the nodes it is the identity (each cardinal function
+    is 1 at its node and 0 at the others); E q equals solve-then-evaluate; E equals LAPACK's
+    solve of the transposed system; a smooth field is reproduced between the nodes."""
+    X = inputs.nodes(642, 1)
+    A = orc.global_matrix(X, kkind, eps)
+    cond = np.linalg.cond(A)
+    tol = 50 * cond * np.finfo(float).eps
+    np.testing.assert_allclose(orc.global_cardinal(X, X, kkind, eps), np.eye(642), atol=tol)
+    P = inputs.random_unit_vectors(300, np.random.default_rng(3))
+    E = orc.global_cardinal(P, X, kkind, eps)
+    assert E.shape == (300, 642)
+    q = np.stack([inputs.gaussian_hills(X, [[0.6, 0.8, 0.0]], 5.0, 0.95), X[:, 0] * X[:, 1]], 1)
+    G = orc.GlobalInterpolator(X, kkind, eps)
+    np.testing.assert_allclose(E @ q, G.apply(P, q), atol=1e-12)
+    Phi = np.array([[orc.kernel(kkind, eps, float(np.linalg.norm(p - x))) for x in X] for p in P[:7]])
+    np.testing.assert_allclose(E[:7], np.linalg.solve(A, Phi.T).T, atol=tol)
+    exact = np.stack([inputs.gaussian_hills(P, [[0.6, 0.8, 0.0]], 5.0, 0.95), P[:, 0] * P[:, 1]], 1)
+    assert np.abs(E @ q - exact).max() < 5e-3
 
 
 def test_global_imq_kernel_matches_definition(orc):
