@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
-    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq", "tceval"],
+    ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq", "tceval",
+                                                  "cardinal"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
     ap.add_argument("--repeat", type=int, default=3)
@@ -298,16 +299,65 @@ def finite_or_none(v):
     return v if np.isfinite(v) else None
 
 
-def global_ctx(rbfsl, w, prec, stream, eps=None):
+def global_ctx(rbfsl, w, prec, stream, eps=None, form=None):
     ctx = rbfsl.Context(0, stream=stream)
     ctx.set_nodes(w.X)
     ctx.set_velocity(w.vel_kind, w.vel_params)
     ctx.set_method(rbfsl.GLOBAL)
     ctx.set_kernel(rbfsl.GAUSS, w.eps if eps is None else eps)
     ctx.set_precision(prec)
+    if form is not None:
+        ctx.set_global_form(form)
     ctx.set_dt(w.dt)
     ctx.set_tracers(w.q0())
     return ctx
+
+
+def bench_global_cardinal(rbfsl, torch, stream, flush, K=5, accuracy_eps=(6.0, 9.0, 24.0)):
+    """The global workload (N = 10,242, 64 tracers, steady tilted rotation) in cardinal form:
+    E = Phi(Xi, X) A_X^-1 formed once (FP64 LU, then 2 N^3 flops of triangular solves), each step
+    q <- E q: 2 N^2 T = 13.4 GFLOP in FP64, or the same terms in FP32-pair arithmetic (~12 FP32
+    operations each, 8.1e10 per step). Peaks derived from GB300's unit counts at 2,070 MHz:
+    FP64 2 DFMA/clk/SM = 1.26 TFLOP/s; FP32 128 lanes/clk/SM = 40.3 T operations/s. Errors after
+    one revolution (200 steps) against the exact solution for several eps."""
+    from paper_1804_01609_gb300 import inputs
+    w = inputs.config_global_rotation()
+    N, T = w.N, w.T
+    terms = float(N) * N * T
+    peaks = {"fp64": 152 * 2 * 2 * 2.07e9, "mixed": 152 * 128 * 2.07e9}
+    work = {"fp64": 2.0 * terms, "mixed": 12.0 * terms}
+    out = {"eps": w.eps, "form": "cardinal"}
+    for prec, name in ((rbfsl.FP64, "fp64"), (rbfsl.MIXED, "mixed")):
+        ctx = global_ctx(rbfsl, w, prec, stream, form=rbfsl.GLOBAL_CARDINAL)
+        t0 = time.perf_counter()
+        ctx.step(1)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        ms = timed_steps(ctx, K, 1, stream, flush, torch)
+        ctx.close()
+        rate = work[name] / (float(ms.mean()) * 1e-3)
+        out[name] = {"value": N / (float(ms.mean()) / 1e3), "ms_per_step": float(ms.mean()),
+                     "setup_and_first_step_s": setup,
+                     ("tflops" if name == "fp64" else "fp32_tops"): rate / 1e12,
+                     "frac_of_derived_peak": rate / peaks[name]}
+    q0 = w.q0()
+    acc = []
+    for eps in accuracy_eps:
+        row = {"eps": eps}
+        qs = {}
+        for prec, name in ((rbfsl.FP64, "fp64"), (rbfsl.MIXED, "mixed")):
+            ctx = global_ctx(rbfsl, w, prec, stream, eps, form=rbfsl.GLOBAL_CARDINAL)
+            ctx.step(w.steps)
+            qs[name] = ctx.get_q()
+            ctx.close()
+            ok = bool(np.isfinite(qs[name]).all())
+            row[name + "_l2_vs_exact"] = finite_or_none(rel_l2(qs[name], q0)) if ok else None
+        if row["fp64_l2_vs_exact"] is not None and row["mixed_l2_vs_exact"] is not None:
+            row["mixed_over_fp64"] = row["mixed_l2_vs_exact"] / row["fp64_l2_vs_exact"]
+            row["mixed_l2_vs_fp64"] = finite_or_none(rel_l2(qs["mixed"], qs["fp64"]))
+        acc.append(row)
+    out["accuracy_after_200_steps"] = acc
+    return out
 
 
 def bench_global(rbfsl, torch, stream, flush, K=3, accuracy_eps=(6.0, 9.0, 24.0)):
@@ -547,6 +597,25 @@ def run_case(args):
         print(f"case tceval: {e0.elapsed_time(e1) / args.repeat:.3f} ms per call (N = Nq = {wg.N}, T = {wg.T})",
               flush=True)
         return
+    if args.case == "cardinal":  # q <- E q at the global workload's size, FP64 and FP32 pairs
+        Ng, Tg = 10242, 64
+        g = torch.Generator(device="cuda").manual_seed(12)
+        for name, shape, dt in (("fp64", (Ng, Ng), torch.float64), ("pairs", (Ng, Ng, 2), torch.float32)):
+            E = torch.randn(shape, generator=g, device="cuda", dtype=dt) / Ng ** 0.5
+            q = torch.randn((Ng, Tg) + shape[2:], generator=g, device="cuda", dtype=dt)
+            o = torch.empty_like(q)
+            ws = rbfsl.rbfsl_cardinal_apply(E, q, o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.repeat):
+                rbfsl.rbfsl_cardinal_apply(E, q, o, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            print(f"case cardinal {name}: {e0.elapsed_time(e1) / args.repeat:.3f} ms per call "
+                  f"(Nq = N = {Ng}, T = {Tg}, workspace {ws.numel()} B)", flush=True)
+            del E, q, o, ws
+        return
     w = workload()
     N, n = w.N, w.n
     nq = min(args.nq, N)
@@ -721,6 +790,8 @@ def main():
     glob = bench_global(rbfsl, torch, stream, flush,
                         accuracy_eps=(6.0, 9.0, 24.0) if args.accuracy_steps > 0 else ())
     glob["evaluation_alone"] = bench_global_eval(rbfsl, torch, stream, flush)
+    glob["cardinal_form"] = bench_global_cardinal(rbfsl, torch, stream, flush,
+                                                  accuracy_eps=(6.0, 9.0, 24.0) if args.accuracy_steps > 0 else ())
     batched = {}
     if not args.no_batched:
         batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),

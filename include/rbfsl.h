@@ -238,6 +238,37 @@ int rbfsl_global_eval_tc(const double *p, int64_t Nq, const double *x, int64_t N
                          double eps, const void *c, int c_dtype, int T, float *out,
                          void *workspace, size_t workspace_bytes, int32_t *status, void *stream);
 
+/* Cardinal matrix of the global interpolant at Nq fixed points (Sec. 2.1): the interpolant of
+ * q at p is phi(p, X) c with A_X c = q (Eqs. srbfinterp, rbf_linsys), so at all the points it
+ * is E q with
+ *   E = Phi(P, X) A_X^-1,   E[i][j] = value at p_i of the cardinal function of node x_j.
+ * Under a steady flow the departure points are the same at every step, and one product
+ * q <- E q (rbfsl_cardinal_apply) replaces the per-step solve and evaluation.
+ *   LU, perm: the factor of rbfsl_global_factor for the same x, kernel and eps (A_X is
+ *   symmetric, so E^T = A_X^-1 Phi(P, X)^T is solved with it in blocks of points).
+ *   x: device N x 3; p: device Nq x 3. E: device Nq x N row-major, e_dtype RBFSL_F64 (doubles)
+ *   or RBFSL_F32X2 (FP32 pairs hi = fl32(e), lo = fl32(e - hi); Nq x N x 2 floats), computed in
+ *   FP64 either way. Allocates and frees 2 N min(Nq, 512) doubles of device scratch and
+ *   synchronises `stream`. Errors: EINVAL (sizes, kernel, dtype, null pointers), ENOMEM, ECUDA. */
+int rbfsl_global_cardinal(const double *LU, const int32_t *perm, const double *x, int64_t N,
+                          int kernel, double eps, const double *p, int64_t Nq, void *E,
+                          int e_dtype, void *stream);
+
+/* q_out = E q for a cardinal matrix E (Nq x N) and T fields q (N x T), row-major:
+ *   q_out[i][t] = sum_j E[i][j] q[j][t].
+ * dtype RBFSL_F64: E, q, q_out doubles, FP64 arithmetic. RBFSL_F32X2: FP32 pairs, each term
+ * formed in pair arithmetic with FP32 operations only (relative rounding ~2^-48 per term; the
+ * cardinal values are O(1), so there is no cancellation to amplify it).
+ * The sum over j is split into ranges so that the grid covers the device; the partial sums go
+ * to `workspace` (at least rbfsl_cardinal_apply_workspace_bytes(Nq, N, T) bytes on the calling
+ * device, 0 when no split is needed; the caller owns it and must not share it between calls that
+ * overlap on the GPU) and are added in a fixed order, so the result is deterministic for a given
+ * device. q_out may not alias q. Asynchronous on `stream`.
+ * Errors: EINVAL (sizes, dtype, null pointers, workspace too small), ECUDA. */
+size_t rbfsl_cardinal_apply_workspace_bytes(int64_t Nq, int64_t N, int T);
+int rbfsl_cardinal_apply(const void *E, int64_t Nq, int64_t N, const void *q, int T, int dtype,
+                         void *q_out, void *workspace, size_t workspace_bytes, void *stream);
+
 /* ================================================================== context (Algorithm 1) */
 typedef struct rbfsl_ctx rbfsl_ctx;
 
@@ -279,6 +310,16 @@ int rbfsl_set_dt(rbfsl_ctx *ctx, double dt);
  * batched and served paths trace with RK4. Errors: EINVAL. */
 enum { RBFSL_RK4 = 4, RBFSL_RK5 = 5 };
 int rbfsl_set_integrator(rbfsl_ctx *ctx, int order);
+/* Form of the RBFSL_GLOBAL step. RBFSL_GLOBAL_SOLVE (default): per step the coefficients
+ * A_X^-1 q and the evaluation at the departure points (Sec. 3.3). RBFSL_GLOBAL_CARDINAL: the
+ * departure points are traced once and E = Phi(Xi, X) A_X^-1 is formed at preparation
+ * (rbfsl_global_cardinal; A_X's factor is freed afterwards), each step is q <- E q
+ * (rbfsl_cardinal_apply: FP64, or FP32-pair arithmetic in RBFSL_MIXED). Valid for a steady
+ * velocity only (RBFSL_VEL_RIGID; the first step returns EINVAL otherwise). Invalidates
+ * prepared state, as do set_dt and set_integrator while the cardinal form is selected (E
+ * depends on the departure points). Errors: EINVAL. */
+enum { RBFSL_GLOBAL_SOLVE = 0, RBFSL_GLOBAL_CARDINAL = 1 };
+int rbfsl_set_global_form(rbfsl_ctx *ctx, int form);
 int rbfsl_set_time(rbfsl_ctx *ctx, double t);
 /* Initial field q(X, t): N x T, element type dtype (converted to the context precision),
  * on the host (copied synchronously) or the device (copied on the context stream).

@@ -73,6 +73,7 @@ struct rbfsl_ctx {
     int precision = RBFSL_FP64;
     double dt = 0.0, t = 0.0;
     int integrator = RBFSL_RK4;
+    int global_form = RBFSL_GLOBAL_SOLVE;
     int T = 0;
     void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 pairs (mixed), 8 bytes each
     int64_t steps_done = 0;
@@ -90,6 +91,9 @@ struct rbfsl_ctx {
     size_t tc_ws_bytes = 0;
     int32_t *dev_err = nullptr;  // RBFSL_ETIMEDOUT from a bounded device wait
     int32_t *perm = nullptr, *piv = nullptr;
+    void *E = nullptr;         // global, cardinal form: Nq x N, FP64 or FP32 pairs
+    void *card_ws = nullptr;   // its split-K partial sums
+    size_t card_ws_bytes = 0;
     int prepared_T = 0;
     // RBF-PU
     double *pu_centers = nullptr;
@@ -148,6 +152,8 @@ void release_prepared(rbfsl_ctx *c) {
     cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->C32); cudaFree(c->perm); cudaFree(c->piv);
     cudaFree(c->tc_ws); cudaFree(c->dev_err);
     c->tc_ws = nullptr; c->tc_ws_bytes = 0; c->dev_err = nullptr;
+    cudaFree(c->E); cudaFree(c->card_ws);
+    c->E = nullptr; c->card_ws = nullptr; c->card_ws_bytes = 0;
     if (c->pu) rbfsl_pu_destroy(c->pu);
     c->pu = nullptr;
     c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
@@ -172,9 +178,12 @@ int effective_ell(const rbfsl_ctx *c) {
 
 // Global method (Sec. 3.3): A_X assembled and factorised once; per step a solve and an
 // evaluation at the departure points.
+int prepare_global_cardinal(rbfsl_ctx *c);
+
 int prepare_global(rbfsl_ctx *c) {
     if (c->kkind != RBFSL_GAUSS && c->kkind != RBFSL_IMQ)
         return fail(c, RBFSL_EINVAL, "the global method needs RBFSL_GAUSS or RBFSL_IMQ");
+    if (c->global_form == RBFSL_GLOBAL_CARDINAL) return prepare_global_cardinal(c);
     const int64_t N = c->N, T = c->T;
     int rc;
     if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
@@ -198,8 +207,46 @@ int prepare_global(rbfsl_ctx *c) {
     return RBFSL_OK;
 }
 
+// Cardinal form (steady flow): departure points traced once, E = Phi(Xi, X) A_X^-1 formed from
+// the factor, which is freed; each step is q <- E q.
+int prepare_global_cardinal(rbfsl_ctx *c) {
+    if (c->vel_kind != RBFSL_VEL_RIGID)
+        return fail(c, RBFSL_EINVAL, "the cardinal form needs a steady velocity field (RBFSL_VEL_RIGID)");
+    const int64_t N = c->N;
+    int rc;
+    if ((rc = dalloc(c, &c->xi, N * 3 * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->LU, N * N * sizeof(double)))) return rc;
+    if ((rc = dalloc(c, &c->perm, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->piv, N * sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->status, sizeof(int32_t)))) return rc;
+    if ((rc = dalloc(c, &c->ctr, 3 * sizeof(unsigned long long)))) return rc;
+    CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
+    if ((rc = dalloc(c, &c->E, N * N * 8))) return rc;
+    c->card_ws_bytes = cardinal_apply_workspace(N, N, c->T);
+    if (c->card_ws_bytes && (rc = dalloc(c, &c->card_ws, c->card_ws_bytes))) return rc;
+    CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, c->t + c->dt, c->dt, RBFSL_FP64, c->integrator,
+                                 c->xi, c->stream));
+    CTX_RC(c, global_factor_full(c->X, N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
+    CTX_RC(c, global_cardinal_build(c->LU, c->perm, c->X, N, c->kkind, c->kparam, c->xi, N, c->E,
+                                    c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2, c->stream));
+    cudaFree(c->LU);
+    c->LU = nullptr;
+    c->bytes -= N * N * sizeof(double);
+    c->prepared_T = c->T;
+    c->prepared = true;
+    return RBFSL_OK;
+}
+
 int one_step_global(rbfsl_ctx *c) {
     const int64_t N = c->N, NT = N * (int64_t)c->T;
+    if (c->global_form == RBFSL_GLOBAL_CARDINAL) {
+        CTX_RC(c, launch_cardinal_apply(c->E, N, N, c->q, c->T, c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2,
+                                        c->q_next, c->card_ws, c->card_ws_bytes, c->stream));
+        std::swap(c->q, c->q_next);
+        c->t += c->dt;
+        ++c->steps_done;
+        return RBFSL_OK;
+    }
     const double t1 = c->t + c->dt;
     const unsigned blocks = (unsigned)((NT + 255) / 256);
     CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, t1, c->dt, c->precision, c->integrator, c->xi, c->stream));
@@ -511,16 +558,39 @@ int rbfsl_set_precision(rbfsl_ctx *c, int precision) {
     return RBFSL_OK;
 }
 
+// The cardinal matrix depends on the departure points: changing them re-prepares.
+static void drop_cardinal(rbfsl_ctx *c) {
+    if (c->method != RBFSL_GLOBAL || c->global_form != RBFSL_GLOBAL_CARDINAL || !c->prepared) return;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    release_prepared(c);
+}
+
 int rbfsl_set_integrator(rbfsl_ctx *c, int order) {
     if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
     if (order != RBFSL_RK4 && order != RBFSL_RK5) return fail(c, RBFSL_EINVAL, "integrator must be RBFSL_RK4 or RBFSL_RK5");
+    if (order != c->integrator) drop_cardinal(c);
     c->integrator = order;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_global_form(rbfsl_ctx *c, int form) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (form != RBFSL_GLOBAL_SOLVE && form != RBFSL_GLOBAL_CARDINAL)
+        return fail(c, RBFSL_EINVAL, "global form must be RBFSL_GLOBAL_SOLVE or RBFSL_GLOBAL_CARDINAL");
+    if (form != c->global_form && c->method == RBFSL_GLOBAL) {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        release_prepared(c);
+    }
+    c->global_form = form;
     return RBFSL_OK;
 }
 
 int rbfsl_set_dt(rbfsl_ctx *c, double dt) {
     if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(c, RBFSL_EINVAL, "dt must be positive");
+    if (dt != c->dt) drop_cardinal(c);
     c->dt = dt;
     return RBFSL_OK;
 }

@@ -22,6 +22,7 @@ DIRECT, CENTER = 0, 1
 PHS, GAUSS, IMQ = 0, 1, 2
 FP64, MIXED = 0, 1
 RK4, RK5 = 4, 5
+GLOBAL_SOLVE, GLOBAL_CARDINAL = 0, 1
 F64, F32, F32X2 = 0, 1, 2
 HOST, DEVICE = 0, 1
 PU_WENDLAND, PU_BSPLINE = 0, 1
@@ -69,6 +70,10 @@ SIGNATURES = {
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
     "rbfsl_global_eval_tc_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
     "rbfsl_global_eval_tc": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P, ctypes.c_size_t, _P, _P]),
+    "rbfsl_global_cardinal": (_I, [_P, _P, _P, _I64, _I, _D, _P, _I64, _P, _I, _P]),
+    "rbfsl_cardinal_apply_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
+    "rbfsl_cardinal_apply": (_I, [_P, _I64, _I64, _P, _I, _I, _P, _P, ctypes.c_size_t, _P]),
+    "rbfsl_set_global_form": (_I, [_P, _I]),
     "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
     "rbfsl_pu_destroy": (_I, [_P]),
     "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
@@ -458,6 +463,39 @@ def rbfsl_global_eval_tc(p, x, kernel, eps, c, out, workspace=None, status=None,
     return workspace
 
 
+def _f64_or_pairs(t):
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32 and t.dim() >= 2 and t.shape[-1] == 2:
+        return F32X2
+    raise TypeError(f"expected float64, or float32 pairs (last dimension 2); got {t.dtype} {tuple(t.shape)}")
+
+
+def rbfsl_global_cardinal(LU, perm, x, kernel, eps, p, E, stream=None):
+    """E = Phi(p, x) A_X^-1 from the factor of rbfsl_global_factor; E: (Nq, N) float64, or
+    (Nq, N, 2) float32 pairs."""
+    _check(load().rbfsl_global_cardinal(_ptr(LU), _ptr(perm), _ptr(x), x.shape[0], kernel, float(eps),
+                                        _ptr(p), p.shape[0], _ptr(E), _f64_or_pairs(E), _stream(stream)))
+
+
+def rbfsl_cardinal_apply(E, q, out, workspace=None, stream=None):
+    """out = E q (FP64, or FP32-pair arithmetic for pair tensors); workspace: a uint8 device
+    tensor (allocated here when None), returned for reuse."""
+    import torch
+    code = _f64_or_pairs(E)
+    if _f64_or_pairs(q) != code or _f64_or_pairs(out) != code:
+        raise TypeError("E, q and out must all be float64 or all FP32 pairs")
+    fdim = 2 if code == F64 else 3
+    T = q.shape[1] if q.dim() == fdim else 1
+    need = load().rbfsl_cardinal_apply_workspace_bytes(E.shape[0], E.shape[1], T)
+    if workspace is None:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=E.device)
+    _check(load().rbfsl_cardinal_apply(_ptr(E), E.shape[0], E.shape[1], _ptr(q), T, code, _ptr(out),
+                                       _ptr(workspace), workspace.numel(), _stream(stream)))
+    return workspace
+
+
 # --------------------------------------------------------------------------- context
 class Context:
     """Algorithm 1 on the device: set the problem, then step. Method names follow the C ABI
@@ -520,6 +558,9 @@ class Context:
 
     def set_integrator(self, order):
         self._c(load().rbfsl_set_integrator(self._h, order))
+
+    def set_global_form(self, form):
+        self._c(load().rbfsl_set_global_form(self._h, form))
 
     def set_time(self, t):
         self._c(load().rbfsl_set_time(self._h, float(t)))
