@@ -12,12 +12,13 @@
 // substitution, as the per-step solve) and transposed into E, FP64 or FP32 pairs.
 //
 // Apply: out = E q, 32 x 64 output tiles per block (eight warps of four rows, two columns per
-// lane), K staged through shared memory in chunks of 32 with cp.async double buffering, split
-// over K so that the grid covers the SMs evenly; the partial sums are added in split order by
-// cardinal_reduce (deterministic). FP64: one DFMA per term, bound by GB300's FP64 rate.
-// FP32 pairs: each term in pair arithmetic (pair_fma, ~12 FP32 operations), bound by the FP32
-// issue rate; the rounding is ~2^-48 relative per term, FP64-like, because the cardinal values
-// are O(1) and do not cancel (unlike the coefficients c, which grow as A_X becomes singular).
+// lane), K staged through shared memory with cp.async double buffering, split over K so that
+// the grid covers the SMs evenly; the partial sums are added in split order by cardinal_reduce
+// (deterministic). FP64: one DFMA per term, bound by GB300's FP64 rate. FP32 pairs: each term
+// in pair arithmetic (pair_fma's 12 FP32 operations), issued as packed FP32x2 instructions for
+// a lane's two columns, bound by the FP32 pipe; the rounding is ~2^-48 relative per term,
+// FP64-like, because the cardinal values are O(1) and do not cancel (unlike the coefficients c,
+// which grow as A_X becomes singular).
 #include <algorithm>
 #include <cmath>
 
@@ -83,36 +84,14 @@ __device__ __forceinline__ void load_two(const double *p, double &a, double &b) 
     a = t.x;
     b = t.y;
 }
-__device__ __forceinline__ void load_two(const float2 *p, float2 &a, float2 &b) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    a = make_float2(t.x, t.y);
-    b = make_float2(t.z, t.w);
-}
 
-// Accumulators: FP64, or an unnormalised FP32 pair (sh, sl).
-struct AccF64 {
-    double v = 0.0;
-    __device__ __forceinline__ void mac(double e, double q) { v = fma(e, q, v); }
-    __device__ __forceinline__ double partial() const { return v; }
-    __device__ __forceinline__ double final_value() const { return v; }
-};
-struct AccPair {
-    float h = 0.0f, l = 0.0f;
-    __device__ __forceinline__ void mac(float2 e, float2 q) { pair_fma(e, q, h, l); }
-    __device__ __forceinline__ float2 partial() const { return make_float2(h, l); }
-    __device__ __forceinline__ float2 final_value() const { return pair_norm(h, l); }
-};
-template <typename V> struct AccOf;
-template <> struct AccOf<double> { using type = AccF64; };
-template <> struct AccOf<float2> { using type = AccPair; };
-
-// out = E q over rows [32 bx, 32 bx + 32), columns [64 by, 64 by + 64) and the K range of split
-// bz. With one split the final values go to `out` (Nq x T); otherwise the accumulators go to
-// part + bz * Nq * T and cardinal_reduce adds them.
-template <typename V>
-__global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_kernel(
-    const V *__restrict__ E, int64_t Nq, int64_t N, const V *__restrict__ q, int T, int64_t kspan,
-    V *__restrict__ out, V *__restrict__ part) {
+// FP64 out = E q over rows [32 bx, 32 bx + 32), columns [64 by, 64 by + 64) and the K range of
+// split bz. With one split the sums go to `out` (Nq x T); otherwise to part + bz * Nq * T, and
+// cardinal_reduce adds them.
+__global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_f64_kernel(
+    const double *__restrict__ E, int64_t Nq, int64_t N, const double *__restrict__ q, int T, int64_t kspan,
+    double *__restrict__ out, double *__restrict__ part) {
+    using V = double;
     __shared__ __align__(16) V Es[2][kApBM][kApBK];
     __shared__ __align__(16) V Qs[2][kApBK][kApCols];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -140,7 +119,7 @@ __global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_kernel(
         }
     };
 
-    typename AccOf<V>::type acc[kApRows][2];
+    double acc[kApRows][2] = {};
     if (nchunks > 0) load(0, kb);
     cp_async_commit();
     for (int ch = 0; ch < nchunks; ++ch) {
@@ -156,8 +135,8 @@ __global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_kernel(
 #pragma unroll
             for (int r = 0; r < kApRows; ++r) {
                 const V e = Es[st][warp * kApRows + r][kk];  // same address in every lane: broadcast
-                acc[r][0].mac(e, q0);
-                acc[r][1].mac(e, q1);
+                acc[r][0] = fma(e, q0, acc[r][0]);
+                acc[r][1] = fma(e, q1, acc[r][1]);
             }
         }
         __syncthreads();  // stage st is refilled by the next iteration's load
@@ -170,8 +149,144 @@ __global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_kernel(
         for (int u = 0; u < 2; ++u) {
             const int c = col0 + 2 * lane + u;
             if (c >= T) continue;
-            if (part) part[(int64_t)blockIdx.z * Nq * T + row * T + c] = acc[r][u].partial();
-            else out[row * T + c] = acc[r][u].final_value();
+            if (part) part[(int64_t)blockIdx.z * Nq * T + row * T + c] = acc[r][u];
+            else out[row * T + c] = acc[r][u];
+        }
+    }
+}
+
+// ---- FP32-pair product with packed FP32x2 instructions. Each lane owns two columns and the
+// pair arithmetic of pair_fma is the same for both, so every operation is issued once for the
+// two columns (add/sub/mul/fma .rn.f32x2: two IEEE round-to-nearest FP32 operations). The
+// shared tiles hold the operands already packed: a cardinal value e as (e.hi, e.hi, e.lo, e.lo)
+// and the two columns' field values as (q0.hi, q1.hi, q0.lo, q1.lo), filled by 4-byte cp.async
+// copies. pe (the exact error of the high product and the cross terms) is carried negated,
+// using the negated field: round-to-nearest is symmetric, so each rounding equals pair_fma's.
+constexpr int kAp2BK = 16;
+typedef unsigned long long f2_t;  // two packed FP32 values, element 0 in the low half
+
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *g, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(g), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// (sh, sl) += e * q for both columns: pair_fma's operations, packed.
+__device__ __forceinline__ void pair_fma2(f2_t ex, f2_t ey, f2_t qh, f2_t nqh, f2_t nql, f2_t &sh, f2_t &sl) {
+    const f2_t p = f2_mul(ex, qh);
+    f2_t npe = f2_fma(ex, nqh, p);  // -(e.hi q.hi - p), exact
+    npe = f2_fma(ex, nql, npe);     // -(pe + e.hi q.lo)
+    npe = f2_fma(ey, nqh, npe);     // -(pe + e.hi q.lo + e.lo q.hi)
+    const f2_t s = f2_add(sh, p);   // two-sum of sh and p
+    const f2_t bp = f2_sub(s, sh);
+    const f2_t err = f2_add(f2_sub(sh, f2_sub(s, bp)), f2_sub(p, bp));
+    sl = f2_add(sl, f2_sub(err, npe));
+    sh = s;
+}
+
+__global__ void __launch_bounds__(kApWarps * 32, 4) cardinal_apply_pair_kernel(
+    const float2 *__restrict__ E, int64_t Nq, int64_t N, const float2 *__restrict__ q, int T, int64_t kspan,
+    float2 *__restrict__ out, float2 *__restrict__ part) {
+    __shared__ __align__(16) float4 Es[3][kApBM][kAp2BK];
+    __shared__ __align__(16) float4 Qs[3][kAp2BK][kApCols / 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t row0 = blockIdx.x * (int64_t)kApBM;
+    const int col0 = blockIdx.y * kApCols;
+    const int64_t kb = blockIdx.z * kspan, ke = std::min<int64_t>(N, kb + kspan);
+    const int nchunks = (int)((ke - kb + kAp2BK - 1) / kAp2BK);
+
+    auto load = [&](int st, int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < kApBM * kAp2BK / (kApWarps * 32); ++u) {
+            const int e = tid + u * kApWarps * 32;
+            const int r = e / kAp2BK, kk = e % kAp2BK;
+            const int64_t row = row0 + r, k = k0 + kk;
+            const bool ok = row < Nq && k < ke;
+            const float *src = ok ? reinterpret_cast<const float *>(E + row * N + k) : reinterpret_cast<const float *>(E);
+            float *dst = reinterpret_cast<float *>(&Es[st][r][kk]);
+            cp_async4(dst + 0, src, ok);
+            cp_async4(dst + 1, src, ok);
+            cp_async4(dst + 2, src + (ok ? 1 : 0), ok);
+            cp_async4(dst + 3, src + (ok ? 1 : 0), ok);
+        }
+#pragma unroll
+        for (int u = 0; u < kAp2BK * kApCols / (kApWarps * 32); ++u) {
+            const int e = tid + u * kApWarps * 32;
+            const int kk = e / kApCols, c = e % kApCols;
+            const int64_t k = k0 + kk;
+            const bool ok = k < ke && col0 + c < T;
+            const float *src = ok ? reinterpret_cast<const float *>(q + k * T + col0 + c) : reinterpret_cast<const float *>(q);
+            float *dst = reinterpret_cast<float *>(&Qs[st][kk][c >> 1]);
+            cp_async4(dst + (c & 1), src, ok);
+            cp_async4(dst + 2 + (c & 1), src + (ok ? 1 : 0), ok);
+        }
+    };
+
+    const f2_t minus_one = 0xBF800000BF800000ull;  // (-1, -1): negation is exact
+    f2_t sh[kApRows], sl[kApRows];
+#pragma unroll
+    for (int r = 0; r < kApRows; ++r) sh[r] = sl[r] = 0ull;
+    // three-stage ring, one barrier per chunk: the barrier that publishes chunk ch also
+    // guarantees that every warp has finished chunk ch - 1, whose stage the load of ch + 2 reuses
+    if (nchunks > 0) load(0, kb);
+    cp_async_commit();
+    if (nchunks > 1) load(1, kb + kAp2BK);
+    cp_async_commit();
+    int st = 0;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        cp_async_wait1();  // this thread's copies of chunk ch have landed
+        __syncthreads();
+        if (ch + 2 < nchunks) load(st == 0 ? 2 : st - 1, kb + (int64_t)(ch + 2) * kAp2BK);
+        cp_async_commit();
+#pragma unroll
+        for (int kk = 0; kk < kAp2BK; ++kk) {
+            const ulonglong2 qv = *reinterpret_cast<const ulonglong2 *>(&Qs[st][kk][lane]);
+            const f2_t nqh = f2_mul(qv.x, minus_one), nql = f2_mul(qv.y, minus_one);
+#pragma unroll
+            for (int r = 0; r < kApRows; ++r) {
+                const ulonglong2 ev = *reinterpret_cast<const ulonglong2 *>(&Es[st][warp * kApRows + r][kk]);
+                pair_fma2(ev.x, ev.y, qv.x, nqh, nql, sh[r], sl[r]);
+            }
+        }
+        st = st == 2 ? 0 : st + 1;
+    }
+#pragma unroll
+    for (int r = 0; r < kApRows; ++r) {
+        const int64_t row = row0 + warp * kApRows + r;
+        if (row >= Nq) continue;
+        float h[2], l[2];
+        f2_unpack(sh[r], h[0], h[1]);
+        f2_unpack(sl[r], l[0], l[1]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = col0 + 2 * lane + u;
+            if (c >= T) continue;
+            if (part) part[(int64_t)blockIdx.z * Nq * T + row * T + c] = make_float2(h[u], l[u]);
+            else out[row * T + c] = pair_norm(h[u], l[u]);
         }
     }
 }
@@ -278,12 +393,12 @@ int launch_cardinal_apply(const void *E, int64_t Nq, int64_t N, const void *q, i
     const int64_t cnt = Nq * (int64_t)T;
     const unsigned rb = (unsigned)((cnt + 255) / 256);
     if (dtype == RBFSL_F64) {
-        cardinal_apply_kernel<double><<<grid, kApWarps * 32, 0, s>>>((const double *)E, Nq, N, (const double *)q, T,
-                                                                    p.kspan, (double *)out, (double *)part);
+        cardinal_apply_f64_kernel<<<grid, kApWarps * 32, 0, s>>>((const double *)E, Nq, N, (const double *)q, T,
+                                                                p.kspan, (double *)out, (double *)part);
         if (part) cardinal_reduce_f64<<<rb, 256, 0, s>>>((const double *)part, cnt, p.S, (double *)out);
     } else {
-        cardinal_apply_kernel<float2><<<grid, kApWarps * 32, 0, s>>>((const float2 *)E, Nq, N, (const float2 *)q, T,
-                                                                    p.kspan, (float2 *)out, (float2 *)part);
+        cardinal_apply_pair_kernel<<<grid, kApWarps * 32, 0, s>>>((const float2 *)E, Nq, N, (const float2 *)q, T,
+                                                                 p.kspan, (float2 *)out, (float2 *)part);
         if (part) cardinal_reduce_pair<<<rb, 256, 0, s>>>((const float2 *)part, cnt, p.S, (float2 *)out);
     }
     return launch_status("cardinal_apply");
