@@ -9,6 +9,9 @@ leg may import it. It shares no code with the CUDA path: the arithmetic lives in
 Parity status of each function (what pins it, see tests/test_oracle_*.py):
   trace_rk4          Rodrigues closed form (rigid rotation), exact y-axis rotation
                      (deformation), fifth-order local error, return after a period
+  velocity (kind 2)  the paper's deformational flow in spherical form: x cross grad(psi) for
+                     its stream function (central differences), tangency, pure rotation at
+                     t = T/2, hand-evaluated values, return of the flow map at t = T
   knn                numpy lexsort of all distances (library sort), scipy cKDTree distances
   sh_eval            scipy.special.sph_harm_y, quadrature orthonormality
   gepp_solve         numpy.linalg.solve (LAPACK dgesv), pivot-order invariance
@@ -150,6 +153,8 @@ def exact_departure(P, kind, prm, t0, t1):
     P = _f64(P)
     if kind == 0:
         return rotate(P, prm[:3], -prm[3] * (t1 - t0))
+    if kind != 1:
+        raise ValueError("no closed-form flow map for this velocity kind")
     kappa, T = prm[0], prm[1]
     y = P[:, 1]
     beta = 2 * kappa * y * (T / math.pi) * (math.sin(math.pi * t0 / T) - math.sin(math.pi * t1 / T))

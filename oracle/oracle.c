@@ -48,11 +48,29 @@ void orc_velocity(int kind, const double *prm, const double *x, double t, double
         u[0] = w1 * x[2] - w2 * x[1];
         u[1] = w2 * x[0] - w0 * x[2];
         u[2] = w0 * x[1] - w1 * x[0];
-    } else {
+    } else if (kind == 1) {
         double g = 2.0 * prm[0] * x[1] * cos(ORC_PI * t / prm[1]);
         u[0] = -g * x[2];
         u[1] = 0.0;
         u[2] = g * x[0];
+    } else {
+        /* Deformational flow of Sec. 4.2 (prm = {kappa, T}) in the paper's spherical form,
+         * lambda = longitude, theta = latitude, lp = lambda - 2 pi t / T:
+         *   u = kappa cos(pi t / T) sin^2(lp) sin(2 theta) + (2 pi / T) cos(theta)
+         *   v = kappa cos(pi t / T) sin(2 lp) cos(theta)
+         * converted to Cartesian with e_lambda = (-sin l, cos l, 0) and
+         * e_theta = (-sin th cos l, -sin th sin l, cos th). */
+        const double T = prm[1];
+        const double lam = atan2(x[1], x[0]);
+        const double th = atan2(x[2], sqrt(x[0] * x[0] + x[1] * x[1]));
+        const double k = prm[0] * cos(ORC_PI * t / T);
+        const double lp = lam - 2.0 * ORC_PI * t / T;
+        const double uu = k * sin(lp) * sin(lp) * sin(2.0 * th) + 2.0 * ORC_PI / T * cos(th);
+        const double vv = k * sin(2.0 * lp) * cos(th);
+        const double sl = sin(lam), cl = cos(lam), st = sin(th), ct = cos(th);
+        u[0] = -uu * sl - vv * st * cl;
+        u[1] = uu * cl - vv * st * sl;
+        u[2] = vv * ct;
     }
 }
 

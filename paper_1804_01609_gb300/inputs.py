@@ -21,6 +21,7 @@ import numpy as np
 # Velocity kinds (must match RBFSL_VEL_* in include/rbfsl.h).
 VEL_RIGID = 0      # u = omega * (a x x): solid-body rotation about unit axis a
 VEL_DEFORM_Y2 = 1  # u = x cross grad(psi), psi = kappa * y^2 * cos(pi t / T)
+VEL_NL = 2         # the paper's deformational flow (Sec. 4.2), params {kappa, T}
 
 SEED_BASE = 1804 * 100
 
@@ -77,6 +78,18 @@ def tilted_axis(tilt: float) -> np.ndarray:
 def deformation_params(kappa: float = 2.4, T: float = 1.0) -> np.ndarray:
     """[kappa, T] for psi = kappa * y^2 * cos(pi t / T)."""
     return np.array([kappa, T], dtype=np.float64)
+
+
+def nl_deformation_params(T: float = 5.0) -> np.ndarray:
+    """[kappa, T] of the paper's deformational flow (Sec. 4.2): kappa = 10 / T, T = 5."""
+    return np.array([10.0 / T, T], dtype=np.float64)
+
+
+def sbr_params(alpha: float = math.pi / 2) -> np.ndarray:
+    """Solid-body rotation of the paper's first test (Sec. 4.1), one revolution per 2 pi, at
+    angle alpha to the equator: rotation vector -(0, sin alpha, cos alpha) (at (1, 0, 0) the
+    flow is northward for alpha = pi / 2)."""
+    return rigid_rotation_params([0.0, -math.sin(alpha), -math.cos(alpha)], 2.0 * math.pi)
 
 
 # ----------------------------------------------------------------------------- tracers
@@ -226,6 +239,48 @@ def config_pu_rotation(N: int = 10242, n: int = 100, ell: int = 3, power: int = 
                     power=power, vel_kind=VEL_RIGID,
                     vel_params=rigid_rotation_params(tilted_axis(0.3), 1.0),
                     steps=steps, dt=1.0 / steps, tracers=tr, seed=seed)
+
+
+# The paper's test cases (Sec. 4) on the Fibonacci node sets that stand in for its node files.
+PAPER_P1 = (math.sqrt(3.0) / 2.0, 0.5, 0.0)
+PAPER_P2 = (math.sqrt(3.0) / 2.0, -0.5, 0.0)
+
+
+def config_sbr(N: int, method: str = "local", n: int = 31, ell: int = -1, power: int = -1,
+               steps: int = 20, revolutions: int = 1, eps: float = 0.0,
+               seed: int = SEED_BASE + 6) -> Workload:
+    """Solid-body rotation of the cosine bell of Sec. 4.1: alpha = pi / 2, bell of radius 1/3 at
+    (1, 0, 0), final time 2 pi per revolution, dt = pi / 10 (20 steps per revolution). ell and
+    power default to the paper's rules (ell = floor((sqrt(n) - 1) / 2), r^(2 ell + 1))."""
+    X = nodes(N, seed)
+    if ell < 0:
+        ell = int(math.floor(0.5 * (math.sqrt(n) - 1.0)))
+    if power < 0:
+        power = 2 * ell + 1
+    tr = TracerSet([lambda P: cosine_bell(P, (1.0, 0.0, 0.0), 1.0 / 3.0)])
+    total = steps * revolutions
+    return Workload(f"sbr-cosine-bell N={N} {method} n={n}", N, X, method, n=n, ell=ell, power=power,
+                    eps=eps, vel_kind=VEL_RIGID, vel_params=sbr_params(), steps=total,
+                    dt=2.0 * math.pi / steps, tracers=tr, seed=seed)
+
+
+def config_nl(N: int, ic: str = "cosine", method: str = "local", n: int = 31, ell: int = -1,
+              power: int = -1, steps: int = 50, eps: float = 0.0, seed: int = SEED_BASE + 7) -> Workload:
+    """Deformational flow of Sec. 4.2 (T = 5, dt = 1/10 by default) with the paper's two cosine
+    bells (0.1 + 0.9 (q1 + q2), radius 1/2) or two Gaussian bells (0.95 exp(-5 |x - p|^2)) at
+    p1, p2 = (sqrt(3)/2, +-1/2, 0); the exact solution at t = T is the initial field."""
+    X = nodes(N, seed)
+    if ell < 0:
+        ell = int(math.floor(0.5 * (math.sqrt(n) - 1.0)))
+    if power < 0:
+        power = 2 * ell + 1
+    if ic == "cosine":
+        fn = lambda P: 0.1 + 0.9 * (cosine_bell(P, PAPER_P1, 0.5) + cosine_bell(P, PAPER_P2, 0.5))
+    else:
+        fn = lambda P: gaussian_hills(P, [PAPER_P1, PAPER_P2], 5.0, 0.95)
+    return Workload(f"nl-deformation-{ic} N={N} {method} n={n}", N, X, method, n=n, ell=ell,
+                    power=power, eps=eps, vel_kind=VEL_NL, vel_params=nl_deformation_params(5.0),
+                    steps=steps, dt=5.0 / steps, tracers=TracerSet([fn]), seed=seed)
 
 
 def batched_problems(P: int = 64, seed: int = SEED_BASE + 4):
