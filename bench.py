@@ -439,6 +439,74 @@ def bench_global_eval(rbfsl, torch, stream, flush, K=10):
             "fp64": {"us": 1e3 * t64, "useful_tflops": flop / (t64 * 1e-3) / 1e12}}
 
 
+# ----------------------------------------------------------------------------- paper cases
+def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
+    """The paper's test cases (Sec. 4) on Fibonacci nodes in FP64 with Fehlberg's RK5 tracer,
+    with the error measures of Sec. 4 against the exact solution (the initial field): solid-body
+    rotation of the cosine
+    bell (alpha = pi/2, one revolution, dt = pi/10) and the deformational flow of two cosine
+    bells and of two Gaussian bells (T = 5, dt = 1/10). Local centre stencils n = 31 and 84
+    (ell and the PHS power by the paper's rules) over N, with the order p of err ~ N^(-p/2)
+    fitted without the smallest N as in the paper; RBF-PU (~84 nodes per patch, ell = 3, r^7)
+    on the rotation; the global IMQ interpolant (eps = 5; the paper does not print its eps) in
+    cardinal form on the rotation at N = 10,242, FP64 and mixed. Seconds are wall time of the
+    steps (set-up excluded, as the paper's cost comparison)."""
+    from paper_1804_01609_gb300 import diagnostics, inputs
+
+    def run(w, method, mode=None, precision=rbfsl.FP64, eps=None):
+        ctx = rbfsl.Context(0, stream=stream)
+        ctx.set_nodes(w.X)
+        ctx.set_velocity(w.vel_kind, w.vel_params)
+        ctx.set_precision(precision)
+        ctx.set_integrator(rbfsl.RK5)  # the paper's choice for its experiments (Sec. 3.2)
+        if method == "global":
+            ctx.set_method(rbfsl.GLOBAL)
+            ctx.set_kernel(rbfsl.IMQ, eps)
+            ctx.set_global_form(rbfsl.GLOBAL_CARDINAL)
+        else:
+            ctx.set_method(rbfsl.LOCAL if method == "local" else rbfsl.PU, mode or rbfsl.DIRECT)
+            ctx.set_stencil_size(w.n)
+            ctx.set_sh_degree(w.ell)
+            ctx.set_kernel(rbfsl.PHS, w.power)
+            if method == "pu":
+                ctx.set_pu(inputs.fibonacci_nodes(int(np.ceil(2.5 * w.N / w.n))))
+        ctx.set_dt(w.dt)
+        ctx.set_tracers(w.q0())
+        ctx.step(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step(w.steps - 1)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        q = ctx.get_q()[:, 0]
+        ctx.close()
+        m = diagnostics.error_measures(q, w.q0()[:, 0])
+        m.update({"N": w.N, "steps_s": secs * w.steps / max(w.steps - 1, 1)})
+        return m
+
+    def sweep(mk, method, mode, ns, Nlist):
+        res = {}
+        for n in ns:
+            rows = [run(mk(N, n), method, mode) for N in Nlist]
+            res[f"n{n}"] = {"rows": rows,
+                            "order_l2": diagnostics.convergence_order(Nlist[1:], [r["l2"] for r in rows[1:]]),
+                            "order_linf": diagnostics.convergence_order(Nlist[1:], [r["linf"] for r in rows[1:]])}
+        return res
+
+    out = {"node_sets": "Fibonacci + 1e-3 rad jitter", "precision": "fp64", "tracer": "rk5"}
+    sbr = lambda N, n: inputs.config_sbr(N, n=n)
+    out["sbr_cosine_bell"] = {"local_center": sweep(sbr, "local", rbfsl.CENTER, (31, 84), Ns)}
+    pu = lambda N, n: inputs.config_sbr(N, method="pu", n=n, ell=3, power=7)
+    out["sbr_cosine_bell"]["pu"] = sweep(pu, "pu", None, (84,), Ns[1:])
+    wg = inputs.config_sbr(10242, method="global")
+    out["sbr_cosine_bell"]["global_imq_eps5_cardinal"] = {
+        "fp64": run(wg, "global", eps=5.0), "mixed": run(wg, "global", precision=rbfsl.MIXED, eps=5.0)}
+    for ic in ("cosine", "gaussian"):
+        mk = lambda N, n, ic=ic: inputs.config_nl(N, ic=ic, n=n)
+        out[f"nl_{ic}_bells"] = {"local_center": sweep(mk, "local", rbfsl.CENTER, (31, 84), Ns)}
+    return out
+
+
 # ----------------------------------------------------------------------------- batched
 def bench_batched(rbfsl, torch, stream, precision, steps=2):
     """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
@@ -792,6 +860,7 @@ def main():
     glob["evaluation_alone"] = bench_global_eval(rbfsl, torch, stream, flush)
     glob["cardinal_form"] = bench_global_cardinal(rbfsl, torch, stream, flush,
                                                   accuracy_eps=(6.0, 9.0, 24.0) if args.accuracy_steps > 0 else ())
+    paper_cases = bench_paper_cases(rbfsl, torch, stream) if args.accuracy_steps > 0 else {}
     batched = {}
     if not args.no_batched:
         batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),
@@ -823,6 +892,7 @@ def main():
         "center_stencils": center,
         "integrator_at_dt_1_150": integ,
         "global_N10242_T64": glob,
+        "paper_test_cases": paper_cases,
         "batched_64_problems": batched,
         "served": served,
         "accuracy": acc,

@@ -50,8 +50,18 @@ enum {
  *                      (solid-body rotation, Sec. 4.1, for any axis).
  * RBFSL_VEL_DEFORM_Y2: u = x cross grad(psi), psi = kappa y^2 cos(pi t / T_f);
  *                      params = {kappa, T_f}. Reverses at t = T_f / 2 and returns every
- *                      parcel at t = T_f (a reversing deformational flow, Sec. 4.2). */
-enum { RBFSL_VEL_RIGID = 0, RBFSL_VEL_DEFORM_Y2 = 1 };
+ *                      parcel at t = T_f (a reversing deformational flow).
+ * RBFSL_VEL_NL:        the paper's deformational flow (Sec. 4.2), params = {kappa, T_f}
+ *                      (the paper: T_f = 5, kappa = 10 / T_f); with longitude lambda, latitude
+ *                      theta and lp = lambda - 2 pi t / T_f,
+ *                        u = kappa cos(pi t/T_f) sin^2(lp) sin(2 theta) + (2 pi/T_f) cos(theta),
+ *                        v = kappa cos(pi t/T_f) sin(2 lp) cos(theta)
+ *                      (zonal, meridional), evaluated as x cross grad(psi) with
+ *                      psi = kappa cos(pi t/T_f) (y cos c - x sin c)^2 - (2 pi/T_f) z,
+ *                      c = 2 pi t / T_f. Returns every parcel at t = T_f. The mixed-precision
+ *                      tracers evaluate this field's stages in FP64. Not accepted by the batched
+ *                      path (rbfsl_batch_add). */
+enum { RBFSL_VEL_RIGID = 0, RBFSL_VEL_DEFORM_Y2 = 1, RBFSL_VEL_NL = 2 };
 
 /* Interpolation method (Sec. 3.3). */
 enum { RBFSL_LOCAL = 0, RBFSL_GLOBAL = 1, RBFSL_PU = 2 };

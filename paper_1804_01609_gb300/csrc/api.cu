@@ -464,6 +464,8 @@ int rbfsl_set_nodes(rbfsl_ctx *c, const double *xyz, int64_t N, int mem) {
     return RBFSL_OK;
 }
 
+static void drop_cardinal(rbfsl_ctx *c);
+
 int rbfsl_set_velocity(rbfsl_ctx *c, int kind, const double *params, int nparams) {
     if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
     if (!params) return fail(c, RBFSL_EINVAL, "set_velocity: params is null");
@@ -471,11 +473,12 @@ int rbfsl_set_velocity(rbfsl_ctx *c, int kind, const double *params, int nparams
         if (nparams != 4) return fail(c, RBFSL_EINVAL, "rigid rotation takes 4 parameters");
         const double a = std::sqrt(params[0] * params[0] + params[1] * params[1] + params[2] * params[2]);
         if (!(std::fabs(a - 1.0) < 1e-12)) return fail(c, RBFSL_EINVAL, "rotation axis is not a unit vector");
-    } else if (kind == RBFSL_VEL_DEFORM_Y2) {
+    } else if (kind == RBFSL_VEL_DEFORM_Y2 || kind == RBFSL_VEL_NL) {
         if (nparams != 2 || !(params[1] > 0)) return fail(c, RBFSL_EINVAL, "deformation takes {kappa, T_f > 0}");
     } else {
         return fail(c, RBFSL_EINVAL, "unknown velocity kind");
     }
+    drop_cardinal(c);
     c->vel_kind = kind;
     for (int i = 0; i < 4; ++i) c->vel[i] = i < nparams ? params[i] : 0.0;
     return RBFSL_OK;

@@ -10,18 +10,29 @@ namespace rbfsl {
 template <typename R>
 struct Vel {
     int kind;
-    R p0, p1, p2, p3;  // rigid: a_x, a_y, a_z, omega; deform: kappa, pi / T_f
+    R p0, p1, p2, p3;  // rigid: a_x, a_y, a_z, omega; deform / NL: kappa, pi / T_f
     __device__ __forceinline__ void operator()(R x, R y, R z, R t, R &ux, R &uy, R &uz) const {
         if (kind == RBFSL_VEL_RIGID) {
             const R w0 = p3 * p0, w1 = p3 * p1, w2 = p3 * p2;
             ux = w1 * z - w2 * y;
             uy = w2 * x - w0 * z;
             uz = w0 * y - w1 * x;
-        } else {
+        } else if (kind == RBFSL_VEL_DEFORM_Y2) {
             const R g = R(2) * p0 * y * cos(p1 * t);
             ux = -g * z;
             uy = R(0);
             uz = g * x;
+        } else {
+            // the paper's deformational flow (Sec. 4.2) as u = x cross grad(psi) with
+            // psi = kappa cos(pi t/T) b^2 - (2 pi / T) z, b = y cos c - x sin c, c = 2 pi t / T:
+            // grad(psi) = (-2 k b sin c, 2 k b cos c, -a), a polynomial field, smooth at the poles
+            const R c = R(2) * p1 * t, cc = cos(c), sc = sin(c);
+            const R k2 = R(2) * p0 * cos(p1 * t), a = R(2) * p1;
+            const R b = y * cc - x * sc, q = x * cc + y * sc;
+            const R kbz = k2 * b * z;
+            ux = -a * y - kbz * cc;
+            uy = a * x - kbz * sc;
+            uz = k2 * b * q;
         }
     }
 };
@@ -103,6 +114,10 @@ __device__ __forceinline__ void vel_increment(int kind, float w0, float w1, floa
 __device__ __forceinline__ void rk4_point_mixed(const Vel<double> &u, double xd, double yd, double zd,
                                                 double t1, double h, double &ox, double &oy,
                                                 double &oz) {
+    if (u.kind == RBFSL_VEL_NL) {  // no FP32 increment form for this field: stages in FP64
+        rk4_point_f64(u, xd, yd, zd, t1, h, ox, oy, oz);
+        return;
+    }
     double U0x, U0y, U0z;
     u(xd, yd, zd, t1, U0x, U0y, U0z);
     // time factors of the deformation at t1, t1 + h/2, t1 + h (FP64); unused for rigid rotation
@@ -202,6 +217,10 @@ __device__ __forceinline__ void rk5_point_f64(const Vel<double> &u, double x, do
 // displacement is c_i h U0 + h sum_j a_ij D_j and the step's is h U0 + h sum_i b_i D_i.
 __device__ __forceinline__ void rk5_point_mixed(const Vel<double> &u, double xd, double yd, double zd,
                                                 double t1, double h, double &ox, double &oy, double &oz) {
+    if (u.kind == RBFSL_VEL_NL) {  // no FP32 increment form for this field: stages in FP64
+        rk5_point_f64(u, xd, yd, zd, t1, h, ox, oy, oz);
+        return;
+    }
     double U0x, U0y, U0z;
     u(xd, yd, zd, t1, U0x, U0y, U0z);
     float w0 = 0.f, w1 = 0.f, w2 = 0.f, k2 = 0.f;

@@ -69,7 +69,7 @@ extern "C" int rbfsl_trace_rk4(const double *x, int64_t N, int vel_kind, const d
     using namespace rbfsl;
     RBFSL_CHECK_ARG(N >= 0, "trace_rk4: N < 0");
     RBFSL_CHECK_ARG(N == 0 || (x && xi && vel_params), "trace_rk4: null pointer");
-    RBFSL_CHECK_ARG(vel_kind == RBFSL_VEL_RIGID || vel_kind == RBFSL_VEL_DEFORM_Y2,
+    RBFSL_CHECK_ARG(vel_kind == RBFSL_VEL_RIGID || vel_kind == RBFSL_VEL_DEFORM_Y2 || vel_kind == RBFSL_VEL_NL,
                     "trace_rk4: unknown velocity kind");
     RBFSL_CHECK_ARG(precision == RBFSL_FP64 || precision == RBFSL_MIXED,
                     "trace_rk4: unknown precision");
@@ -81,7 +81,7 @@ extern "C" int rbfsl_trace_rk5(const double *x, int64_t N, int vel_kind, const d
     using namespace rbfsl;
     RBFSL_CHECK_ARG(N >= 0, "trace_rk5: N < 0");
     RBFSL_CHECK_ARG(N == 0 || (x && xi && vel_params), "trace_rk5: null pointer");
-    RBFSL_CHECK_ARG(vel_kind == RBFSL_VEL_RIGID || vel_kind == RBFSL_VEL_DEFORM_Y2,
+    RBFSL_CHECK_ARG(vel_kind == RBFSL_VEL_RIGID || vel_kind == RBFSL_VEL_DEFORM_Y2 || vel_kind == RBFSL_VEL_NL,
                     "trace_rk5: unknown velocity kind");
     RBFSL_CHECK_ARG(precision == RBFSL_FP64 || precision == RBFSL_MIXED, "trace_rk5: unknown precision");
     return launch_trace_order(x, N, vel_kind, vel_params, t1, dt, precision, 5, xi, (cudaStream_t)stream);

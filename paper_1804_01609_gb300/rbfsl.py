@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOTCONF, ENOMEM, ESINGULAR, EUNCOVERED, ETIMEDOUT, ECUDA, EKNN = 0, -1, -2, -3, -4, -5, -6, -7, -8
-VEL_RIGID, VEL_DEFORM_Y2 = 0, 1
+VEL_RIGID, VEL_DEFORM_Y2, VEL_NL = 0, 1, 2
 LOCAL, GLOBAL, PU = 0, 1, 2
 DIRECT, CENTER = 0, 1
 PHS, GAUSS, IMQ = 0, 1, 2

@@ -89,3 +89,22 @@ def test_nl_flow_returns_at_the_final_time(orc):
         errs.append(np.abs(P - X).max())
     assert errs[1] < 1e-4
     assert 10 < errs[0] / errs[1] < 24
+
+
+def test_error_measures_decompose_the_mean_square_error():
+    """Eqs. dissipation + dispersion add up to the mean-square error (with equal weights);
+    a shifted copy is pure dissipation, a scaled copy about the mean keeps the correlation."""
+    from paper_1804_01609_gb300 import diagnostics
+    rng = np.random.default_rng(8)
+    q = rng.standard_normal(1000)
+    qX = q + 0.1 * rng.standard_normal(1000)
+    m = diagnostics.error_measures(qX, q)
+    assert abs(m["dissipation"] + m["dispersion"] - 1.0) < 1e-12
+    m = diagnostics.error_measures(q + 0.25, q)
+    assert abs(m["dissipation"] - 1.0) < 1e-12 and abs(m["dispersion"]) < 1e-12
+    assert abs(m["mass"] - 0.25) < 1e-15
+    m = diagnostics.error_measures(q.mean() + 1.5 * (q - q.mean()), q)
+    assert abs(m["dispersion"]) < 1e-12 and abs(m["mass"]) < 1e-13
+    assert diagnostics.error_measures(q, q)["l2"] == 0.0
+    Ns = [2562, 10242, 40962]
+    assert abs(diagnostics.convergence_order(Ns, [3.0 * N ** -2.0 for N in Ns]) - 4.0) < 1e-12
