@@ -77,11 +77,11 @@ __global__ void batch_trace_kernel(const BatchDesc *__restrict__ d, int np, int6
                         Xi[3 * j + 2]);
 }
 
-// Shared memory of one point. Direct mode: system region (stencil_doubles), stencil (n int),
-// weights (n double), k-NN buffers (cap double + cap int + 1 int). Centre mode: right-hand
-// side and solution (2 m double), k-NN buffers.
+// Shared memory of one point. Direct mode: system region (ldl_doubles), stencil (n int),
+// k-NN buffers (cap double + cap int + 1 int). Centre mode: right-hand side and solution
+// (2 m double), k-NN buffers.
 __host__ __device__ inline int batch_region_doubles(int mode, int n, int m, int ld) {
-    return mode == RBFSL_DIRECT ? stencil_doubles(n, m, ld) + (n + 1) / 2 + n : 2 * m;
+    return mode == RBFSL_DIRECT ? ldl_doubles(n, m) + (n + 1) / 2 : 2 * m;
 }
 __host__ __device__ inline int batch_point_doubles(int mode, int n, int m, int ld, int cap) {
     return batch_region_doubles(mode, n, m, ld) + cap + (cap + 2) / 2;
@@ -131,8 +131,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             if (i >= b.N) continue;
             double *base = sm + (size_t)warp * per;
             double *A = base;
-            int32_t *S = reinterpret_cast<int32_t *>(base + stencil_doubles(n, m, ld));  // direct only
-            double *wv = base + stencil_doubles(n, m, ld) + (n + 1) / 2;                  // direct only
+            int32_t *S = reinterpret_cast<int32_t *>(base + ldl_doubles(n, m));  // direct only
             double *bd = base + batch_region_doubles(b.mode, n, m, ld);
             int *bi = reinterpret_cast<int *>(bd + cap);
             int *cnt = bi + cap;
@@ -144,12 +143,9 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             } else if (b.mode == RBFSL_DIRECT) {
                 for (int j = lane; j < n; j += 32) S[j] = bi[j];
                 __syncwarp();
-                rc = weights_point<1>(A, b.X, S, n, m, ld, b.ell, b.half, px, py, pz, lane);
-                if (rc == RBFSL_OK) {
-                    for (int j = lane; j < n; j += 32) wv[j] = A[j * ld + m];
-                    __syncwarp();
-                    batch_gather(b, wv, S, i, lane);
-                }
+                double *wv = nullptr;
+                rc = weights_point_ldl<1>(A, b.X, S, n, m, b.ell, b.half, px, py, pz, lane, wv);
+                if (rc == RBFSL_OK) batch_gather(b, wv, S, i, lane);
             } else {
                 const int64_t kc = bi[0];
                 const int32_t *Sg = b.Ik + kc * n;
@@ -170,8 +166,7 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
             // four warps per point (direct mode)
             const int64_t i = tile - b.tile0;
             double *A = sm;
-            int32_t *S = reinterpret_cast<int32_t *>(sm + stencil_doubles(n, m, ld));
-            double *wv = sm + stencil_doubles(n, m, ld) + (n + 1) / 2;
+            int32_t *S = reinterpret_cast<int32_t *>(sm + ldl_doubles(n, m));
             double *bd = sm + batch_region_doubles(b.mode, n, m, ld);
             int *bi = reinterpret_cast<int *>(bd + cap);
             int *cnt = bi + cap;
@@ -181,11 +176,10 @@ __global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__res
                 for (int j = lane; j < n; j += 32) S[j] = ok ? bi[j] : -1;
             }
             __syncthreads();
-            const int rc = weights_point<4>(A, b.X, S, n, m, ld, b.ell, b.half, px, py, pz, t);
+            double *wv = nullptr;
+            const int rc = weights_point_ldl<4>(A, b.X, S, n, m, b.ell, b.half, px, py, pz, t, wv);
             if (warp == 0) {
                 if (rc == RBFSL_OK) {
-                    for (int j = lane; j < n; j += 32) wv[j] = A[j * ld + m];
-                    __syncwarp();
                     batch_gather(b, wv, S, i, lane);
                 } else {
                     const int in = (int)(b.step & 1);
@@ -263,7 +257,7 @@ int default_ppt(const rbfsl_batch *b, int n, int ell, int mode) {
     auto it = b->tile_rule.find(class_key(n, ell));
     if (it != b->tile_rule.end()) return it->second;
     const int m = n + (ell + 1) * (ell + 1);
-    return stencil_doubles(n, m, (m + 1) | 1) * 8 > 40 * 1024 ? 1 : 4;  // the single-problem rule
+    return ldl_doubles(n, m) * 8 > kWeightsSmallBytes ? 1 : 4;  // the single-problem rule
 }
 
 void free_problem(HostProblem &h) {

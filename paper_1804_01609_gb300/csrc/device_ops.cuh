@@ -620,6 +620,258 @@ __device__ __forceinline__ int weights_point(double *__restrict__ A, const doubl
     }
 }
 
+// ---- Weights by symmetric indefinite factorisation. The saddle-point matrix
+// A~ = [[A, P], [P^T, 0]] of Eq. rbf_poly_linsys is symmetric, so A~ w~ = b is solved by
+// P A~ P^T = L D L^T with Bunch-Kaufman pivoting (1 x 1 and 2 x 2 pivots, symmetric
+// interchanges): m^3 / 6 FMAs instead of elimination's m^3 / 3, on the lower triangle only.
+// The PHS block has a zero diagonal, so the first pivots are 2 x 2.
+//
+// Shared region of one point (doubles): the packed lower triangle (element (i, j), j <= i, at
+// i (i + 1) / 2 + j), the right-hand side / solution y (m), the step vectors u0, u1 (the pivot
+// columns before scaling) and l0, l1 (the multipliers), the stencil coordinates (3 n; the
+// weights on return), then ints: the position -> stencil-row map (m), the pivot kinds (m) and
+// four words of step state.
+__host__ __device__ inline int ldl_doubles(int n, int m) {
+    return m * (m + 1) / 2 + 5 * m + 3 * n + (2 * m + 4 + 1) / 2;
+}
+// Shared-memory bytes of one point up to which one warp takes a point (m <~ 45).
+constexpr int kWeightsSmallBytes = 12 * 1024;
+
+__device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+
+// Row of flat index e in a lower triangle of rows of 1, 2, 3, ... elements.
+__device__ __forceinline__ int tri_row(int e) {
+    int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    if (tri(r) > e) --r;
+    if (tri(r + 1) <= e) ++r;
+    return r;
+}
+
+// Weights of one point by a group of NW warps (thread t of the group). Assembles the packed
+// lower triangle of A~ and b (Eqs. rbf_poly, rbf_poly_linsys), factorises with Bunch-Kaufman
+// pivoting (alpha = (1 + sqrt 17) / 8; column maximum lambda at row r (smaller row on a tie),
+// row maximum sigma of r: 1 x 1 pivot k if |a_kk| >= alpha lambda or |a_kk| sigma >=
+// alpha lambda^2, 1 x 1 pivot r if |a_rr| >= alpha sigma, else the 2 x 2 pivot (k, r)),
+// applying the forward substitution to b as it goes, then solves D and L^T. Warp 0 takes the
+// pivot decisions, interchanges and multipliers; all warps update the trailing triangle, each
+// element by the same FMAs whichever thread takes it, so any NW gives the same bits. Returns
+// RBFSL_OK with the weights w (n doubles, stencil order) in `out` (valid for warp 0),
+// RBFSL_EKNN for a stencil index < 0, RBFSL_ESINGULAR for two coincident stencil nodes or a
+// zero or non-finite pivot.
+template <int NW>
+__device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const double *__restrict__ X,
+                                                 const int32_t *__restrict__ stencil, int n, int m, int ell,
+                                                 int half, double px, double py, double pz, int t,
+                                                 double *&out) {
+    constexpr int GT = NW * kWarp;
+    constexpr double kAlpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
+    const int warp = t >> 5, lane = t & 31;
+    const int M = m - n;
+    double *P = R, *y = P + tri(m), *u0 = y + m, *u1 = u0 + m, *l0 = u1 + m, *l1 = l0 + m;
+    double *cx = l1 + m, *cy = cx + n, *cz = cy + n;
+    int *perm = reinterpret_cast<int *>(cz + n), *ptype = perm + m, *st = ptype + m;
+    // st[0]: error flag, st[1]: pivot size of the current step
+    auto gsync = [] {
+        if (NW == 1) __syncwarp(); else __syncthreads();
+    };
+    out = cx;
+    if (t == 0) st[0] = 0;
+    gsync();
+    for (int j = t; j < n; j += GT) {
+        const int64_t s = stencil[j];
+        if (s < 0) { st[0] = 1; continue; }  // a failed neighbour search leaves -1
+        cx[j] = X[3 * s];
+        cy[j] = X[3 * s + 1];
+        cz[j] = X[3 * s + 2];
+    }
+    gsync();
+    if (st[0]) return RBFSL_EKNN;
+
+    // ---- assembly of the lower triangle; the n(n-1)/2 pairs folded into rows of n-1
+    const int P2 = n * (n - 1) / 2;
+    for (int p = t; p < P2; p += GT) {
+        const int f = p / (n - 1), e = p - f * (n - 1);
+        int r, c;
+        if (e < n - 1 - f) { r = f + 1 + e; c = f; } else { r = e + 1; c = n - 1 - f; }
+        const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 == 0.0) st[0] = 2;  // two coincident nodes: two equal rows, singular
+        P[tri(r) + c] = phs_from_d2(d2, half);
+    }
+    for (int j = t; j < n; j += GT) {
+        P[tri(j) + j] = 0.0;
+        sh_eval(ell, cx[j], cy[j], cz[j], [&](int c, double v) { P[tri(n + c) + j] = v; });
+        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
+        y[j] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
+    }
+    for (int e = t; e < tri(M); e += GT) {
+        const int a = tri_row(e);
+        P[tri(n + a) + n + (e - tri(a))] = 0.0;
+    }
+    for (int p = t; p < m; p += GT) perm[p] = p;
+    if (warp == 0) sh_eval_lanes(ell, px, py, pz, lane, [&](int c, double v) { y[n + c] = v; });
+    gsync();
+    if (st[0]) return RBFSL_ESINGULAR;
+
+    for (int k = 0; k < m;) {
+        if (warp == 0) {
+            // ---- pivot decision: lambda = max |a_ik| below the diagonal, r its row
+            long long best = -1;
+            int r = m;
+            for (int i = k + 1 + lane; i < m; i += kWarp) {
+                const long long v = __double_as_longlong(P[tri(i) + k]) & 0x7fffffffffffffffLL;
+                if (v > best) { best = v; r = i; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, r, off);
+                if (ob > best || (ob == best && oi < r)) { best = ob; r = oi; }
+            }
+            const double lam = best < 0 ? 0.0 : __longlong_as_double(best);
+            const double akk = fabs(P[tri(k) + k]);
+            int s = 1, piv = k;
+            if (!(akk >= kAlpha * lam)) {
+                double sg = 0.0;  // sigma: max off-diagonal |a| in row / column r
+                for (int c = k + lane; c < m; c += kWarp)
+                    if (c != r) sg = fmax(sg, fabs(c < r ? P[tri(r) + c] : P[tri(c) + r]));
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) sg = fmax(sg, __shfl_xor_sync(0xffffffffu, sg, off));
+                if (akk * sg >= kAlpha * lam * lam) {
+                    s = 1;
+                } else if (fabs(P[tri(r) + r]) >= kAlpha * sg) {
+                    piv = r;
+                } else {
+                    s = 2;
+                    piv = r;
+                }
+            }
+            // ---- symmetric interchange of positions a < b (lower triangle, L rows included)
+            const int a = s == 1 ? k : k + 1, b = piv;
+            if (b != a) {
+                for (int c = lane; c < m; c += kWarp) {
+                    double *p1, *p2;
+                    if (c < a) { p1 = &P[tri(a) + c]; p2 = &P[tri(b) + c]; }
+                    else if (c == a) { p1 = &P[tri(a) + a]; p2 = &P[tri(b) + b]; }
+                    else if (c < b) { p1 = &P[tri(c) + a]; p2 = &P[tri(b) + c]; }
+                    else if (c == b) continue;
+                    else { p1 = &P[tri(c) + a]; p2 = &P[tri(c) + b]; }
+                    const double v = *p1;
+                    *p1 = *p2;
+                    *p2 = v;
+                }
+                if (lane == 0) {
+                    const double v = y[a]; y[a] = y[b]; y[b] = v;
+                    const int q = perm[a]; perm[a] = perm[b]; perm[b] = q;
+                }
+                __syncwarp();
+            }
+            // ---- multipliers of the trailing rows
+            if (s == 1) {
+                const double d = P[tri(k) + k];
+                const bool bad = !(d != 0.0) || !isfinite(d);
+                const double dinv = 1.0 / d;
+                for (int i = k + 1 + lane; i < m; i += kWarp) {
+                    const double c = P[tri(i) + k];
+                    u0[i] = c;
+                    const double l = c * dinv;
+                    l0[i] = l;
+                    P[tri(i) + k] = l;
+                }
+                if (lane == 0) { ptype[k] = 1; st[1] = 1; if (bad) st[0] = 2; }
+            } else {
+                const double a11 = P[tri(k) + k], a21 = P[tri(k + 1) + k], a22 = P[tri(k + 1) + k + 1];
+                const double det = a11 * a22 - a21 * a21;
+                const bool bad = !(det != 0.0) || !isfinite(det);
+                const double idet = 1.0 / det;
+                for (int i = k + 2 + lane; i < m; i += kWarp) {
+                    const double c0 = P[tri(i) + k], c1 = P[tri(i) + k + 1];
+                    u0[i] = c0;
+                    u1[i] = c1;
+                    const double L0 = (c0 * a22 - c1 * a21) * idet, L1 = (c1 * a11 - c0 * a21) * idet;
+                    l0[i] = L0;
+                    l1[i] = L1;
+                    P[tri(i) + k] = L0;
+                    P[tri(i) + k + 1] = L1;
+                }
+                if (lane == 0) { ptype[k] = 2; ptype[k + 1] = 0; st[1] = 2; if (bad) st[0] = 2; }
+            }
+            if (lane == 0 && lam == 0.0 && akk == 0.0) st[0] = 2;  // a zero column: singular
+        }
+        gsync();
+        if (st[0]) return RBFSL_ESINGULAR;
+        // ---- trailing update, rows and columns base..m-1 (lower triangle), and the rhs. Each
+        // thread takes four elements of the flattened triangle at a time (all loads, then the
+        // FMAs, then the stores) so that several DFMAs per warp are in flight.
+        const int s = st[1], base = k + s, Rr = m - base, E = Rr * (Rr + 1) / 2;
+        constexpr int U = 4;
+        for (int e0 = t; e0 < E; e0 += U * GT) {
+            int addr[U], ii[U], jj[U];
+            double v[U], a0[U], b0[U], a1[U], b1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * GT;
+                const int ec = e < E ? e : E - 1;  // out-of-range slots repeat a valid load
+                const int tt = tri_row(ec);
+                ii[u] = base + tt;
+                jj[u] = base + (ec - tri(tt));
+                addr[u] = tri(ii[u]) + jj[u];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                v[u] = P[addr[u]];
+                a0[u] = l0[ii[u]];
+                b0[u] = u0[jj[u]];
+                if (s == 2) { a1[u] = l1[ii[u]]; b1[u] = u1[jj[u]]; }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e0 - lane + u * GT >= E) continue;  // the whole warp past the end: no DFMA issued
+                v[u] = fma(-a0[u], b0[u], v[u]);
+                if (s == 2) v[u] = fma(-a1[u], b1[u], v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (e0 + u * GT < E) P[addr[u]] = v[u];
+        }
+        {
+            const double yk0 = y[k], yk1 = s == 2 ? y[k + 1] : 0.0;
+            for (int i = base + t; i < m; i += GT) {
+                double v = fma(-l0[i], yk0, y[i]);
+                if (s == 2) v = fma(-l1[i], yk1, v);
+                y[i] = v;
+            }
+        }
+        gsync();
+        k = base;
+    }
+    if (warp != 0) return RBFSL_OK;
+    // ---- D z = y (blocks independent), then L^T x = z column by column
+    for (int p = lane; p < m; p += kWarp) {
+        if (ptype[p] == 1) {
+            y[p] = y[p] / P[tri(p) + p];
+        } else if (ptype[p] == 2) {
+            const double a11 = P[tri(p) + p], a21 = P[tri(p + 1) + p], a22 = P[tri(p + 1) + p + 1];
+            const double det = a11 * a22 - a21 * a21;
+            const double y0 = y[p], y1 = y[p + 1];
+            y[p] = (a22 * y0 - a21 * y1) / det;
+            y[p + 1] = (a11 * y1 - a21 * y0) / det;
+        }
+    }
+    __syncwarp();
+    for (int j = m - 1; j > 0; --j) {
+        const double xj = y[j];
+        const int skip = ptype[j] == 0 ? j - 1 : -1;  // (j-1, j) is a 2 x 2 block: no L entry
+        for (int i = lane; i < j; i += kWarp)
+            if (i != skip) y[i] = fma(-P[tri(j) + i], xj, y[i]);
+        __syncwarp();
+    }
+    for (int p = lane; p < m; p += kWarp)
+        if (perm[p] < n) out[perm[p]] = y[p];
+    __syncwarp();
+    return RBFSL_OK;
+}
+
 // Centre-stencil weights of one point by one warp (Sec. 3.3): the point uses the stencil
 // S = Ik[k] of its nearest node k, whose m x m saddle-point matrix was factorised once. Ft is
 // that factor stored column-major, the upper columns scaled by the reciprocal diagonal

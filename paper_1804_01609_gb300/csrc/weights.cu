@@ -1,14 +1,14 @@
 // Stencil weights of the augmented local RBF interpolant (Sec. 2.2, Eqs. rbf_poly and
-// rbf_poly_linsys), one warp per evaluation point, FP64 throughout.
+// rbf_poly_linsys), FP64 throughout.
 //
-// The warp assembles the (n + M) x (n + M + 1) augmented saddle-point system in shared
-// memory (M = (ell+1)^2):
-//     [ A    P  | phi(|p - x_j|) ]      A_jk = |x_j - x_k|^pw   (PHS, zero diagonal)
-//     [ P^T  0  | Y(p)           ]      P_jc = Y_c(x_j)
-// and eliminates it with partial pivoting (largest magnitude, smaller row on a tie; the
-// pivot search is a warp-shuffle arg-max). Lanes own columns during the rank-1 updates, so
-// the pivot row lives in registers and each update is one shared-memory load, one DFMA and
-// one store. GB300's FP64 rate is the roofline of this kernel: ~(2/3) m^3 flops per point.
+// Each point's group of warps assembles the lower triangle of the symmetric (n + M) x (n + M)
+// saddle-point system in shared memory (M = (ell+1)^2):
+//     [ A    P ] w~ = [ phi(|p - x_j|) ]      A_jk = |x_j - x_k|^pw   (PHS, zero diagonal)
+//     [ P^T  0 ]      [ Y(p)           ]      P_jc = Y_c(x_j)
+// and solves it by a Bunch-Kaufman L D L^T factorisation (weights_point_ldl): ~m^3 / 3 flops
+// per point, half of Gaussian elimination's, bound by GB300's FP64 rate. Small systems take one
+// warp per point (four points per block); larger ones four (or eight) warps per point, several
+// points per SM so that one point's pivot decisions overlap the others' updates.
 #include <cstdlib>
 
 #include "common.cuh"
@@ -56,15 +56,14 @@ struct WeightsArgs {
     const double *X;
     const int32_t *idx;
     int64_t Nq;
-    int n, ell, half, m, ld;
-    int stencil_doubles;  // shared-memory doubles per point
+    int n, ell, half, m;
+    int region_doubles;  // shared-memory doubles per point
     const double *P;
     int32_t *status;
 };
 
-// NW warps per point (1, 4, 5, 8 or 9). With NW = 1 a block holds blockDim/32 independent points and
+// NW warps per point (1, 4 or 8). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW > 1 a block is one point and uses __syncthreads.
-// NW = 5 or 9: four or eight warps for the trailing updates and a pivot warp (look-ahead).
 template <int NW, typename WT>
 __global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
     extern __shared__ double smem[];
@@ -73,20 +72,24 @@ __global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32) weights_kernel(Weight
     const int spb = blockDim.x / GT;
     const int64_t i = (int64_t)blockIdx.x * spb + g;
     if (i >= a.Nq) return;  // NW == 1 only (with NW > 1 the grid has exactly Nq blocks)
-    double *A = smem + (size_t)g * a.stencil_doubles;
-    const int rc = weights_point<NW>(A, a.X, a.idx + i * a.n, a.n, a.m, a.ld, a.ell, a.half,
-                                     a.P[3 * i], a.P[3 * i + 1], a.P[3 * i + 2], t);
+    double *R = smem + (size_t)g * a.region_doubles;
+    double *w = nullptr;
+    const int rc = weights_point_ldl<NW>(R, a.X, a.idx + i * a.n, a.n, a.m, a.ell, a.half,
+                                         a.P[3 * i], a.P[3 * i + 1], a.P[3 * i + 2], t, w);
     if (t >= kWarp) return;
     const int n = a.n, lane = t;
-    for (int j = lane; j < n; j += kWarp) W[i * n + j] = wcast<WT>(rc == RBFSL_OK ? A[j * a.ld + a.m] : (double)NAN);
+    for (int j = lane; j < n; j += kWarp) W[i * n + j] = wcast<WT>(rc == RBFSL_OK ? w[j] : (double)NAN);
     if (a.status && lane == 0) a.status[i] = rc;
 }
 
 template <int NW, typename WT>
 int launch_weights_nw(const WeightsArgs &a, int spb, void *w, cudaStream_t s) {
-    const int smem = spb * a.stencil_doubles * 8;
+    const int smem = spb * a.region_doubles * 8;
     RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_kernel<NW, WT>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // all of the unified L1 / shared storage as shared memory: as many points per SM as fit
+    RBFSL_CUDA_TRY(cudaFuncSetAttribute(weights_kernel<NW, WT>,
+                                        cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     const unsigned blocks = (unsigned)((a.Nq + spb - 1) / spb);
     weights_kernel<NW, WT><<<blocks, spb * NW * kWarp, smem, s>>>(a, (WT *)w);
     return launch_status("stencil_weights");
@@ -108,24 +111,17 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     a.X = x; a.idx = idx; a.Nq = Nq; a.n = n; a.ell = ell; a.half = (power - 1) / 2;
     a.P = p; a.status = status;
     a.m = n + (ell + 1) * (ell + 1);
-    a.ld = (a.m + 1) | 1;  // odd stride: column accesses hit distinct banks
-    a.stencil_doubles = stencil_doubles(n, a.m, a.ld);
-    const int bytes = a.stencil_doubles * 8;
-    if (bytes > 40 * 1024) {
-        // large systems (m >~ 70): several warps per point so that every SM sub-partition's
-        // FP64 unit is fed although only one or two points fit in shared memory. Default: eight
-        // warps of trailing updates plus a pivot warp (look-ahead; 288 threads, two points per
-        // SM); RBFSL_WEIGHTS_WARPS=5 selects four plus the pivot warp, 4 or 8 that many warps
-        // with the pivot search between the updates.
+    a.region_doubles = ldl_doubles(n, a.m);
+    const int bytes = a.region_doubles * 8;
+    if (bytes > kWeightsSmallBytes) {
+        // larger systems (m >~ 45): four warps per point (RBFSL_WEIGHTS_WARPS=8: eight), one
+        // point per block, as many blocks per SM as shared memory allows (four at m = 109)
         static const int nw = [] {
             const char *e = getenv("RBFSL_WEIGHTS_WARPS");
-            const int v = e ? atoi(e) : 9;
-            return (v == 4 || v == 5 || v == 8) ? v : 9;
+            return (e && atoi(e) == 8) ? 8 : 4;
         }();
-        if (nw == 9) return launch_weights_typed<9>(a, 1, w, w_dtype, s);
         if (nw == 8) return launch_weights_typed<8>(a, 1, w, w_dtype, s);
-        if (nw == 4) return launch_weights_typed<4>(a, 1, w, w_dtype, s);
-        return launch_weights_typed<5>(a, 1, w, w_dtype, s);
+        return launch_weights_typed<4>(a, 1, w, w_dtype, s);
     }
     return launch_weights_typed<1>(a, 4, w, w_dtype, s);  // four independent points (warps) per block
 }
