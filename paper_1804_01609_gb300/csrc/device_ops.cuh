@@ -732,11 +732,19 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
             const double akk = fabs(P[tri(k) + k]);
             int s = 1, piv = k;
             if (!(akk >= kAlpha * lam)) {
-                double sg = 0.0;  // sigma: max off-diagonal |a| in row / column r
-                for (int c = k + lane; c < m; c += kWarp)
-                    if (c != r) sg = fmax(sg, fabs(c < r ? P[tri(r) + c] : P[tri(c) + r]));
+                // sigma: max off-diagonal |a| in row / column r (integer compare of the bits)
+                long long sb = 0;
+                for (int c = k + lane; c < m; c += kWarp) {
+                    if (c == r) continue;
+                    const long long v = __double_as_longlong(c < r ? P[tri(r) + c] : P[tri(c) + r]) & 0x7fffffffffffffffLL;
+                    sb = v > sb ? v : sb;
+                }
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) sg = fmax(sg, __shfl_xor_sync(0xffffffffu, sg, off));
+                for (int off = 16; off > 0; off >>= 1) {
+                    const long long o = __shfl_xor_sync(0xffffffffu, sb, off);
+                    sb = o > sb ? o : sb;
+                }
+                const double sg = __longlong_as_double(sb);
                 if (akk * sg >= kAlpha * lam * lam) {
                     s = 1;
                 } else if (fabs(P[tri(r) + r]) >= kAlpha * sg) {
@@ -770,7 +778,9 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
             if (s == 1) {
                 const double d = P[tri(k) + k];
                 const bool bad = !(d != 0.0) || !isfinite(d);
-                const double dinv = 1.0 / d;
+                double dinv = 0.0;
+                if (lane == 0) dinv = 1.0 / d;  // one division, broadcast
+                dinv = __shfl_sync(0xffffffffu, dinv, 0);
                 for (int i = k + 1 + lane; i < m; i += kWarp) {
                     const double c = P[tri(i) + k];
                     u0[i] = c;
@@ -783,7 +793,9 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
                 const double a11 = P[tri(k) + k], a21 = P[tri(k + 1) + k], a22 = P[tri(k + 1) + k + 1];
                 const double det = a11 * a22 - a21 * a21;
                 const bool bad = !(det != 0.0) || !isfinite(det);
-                const double idet = 1.0 / det;
+                double idet = 0.0;
+                if (lane == 0) idet = 1.0 / det;
+                idet = __shfl_sync(0xffffffffu, idet, 0);
                 for (int i = k + 2 + lane; i < m; i += kWarp) {
                     const double c0 = P[tri(i) + k], c1 = P[tri(i) + k + 1];
                     u0[i] = c0;
