@@ -131,14 +131,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
-# capture of this kernel version (profiles/weights_direct_N40962_n84.md).
-WEIGHTS_DRAM_BYTES = 16.26e6
+# capture of this kernel version (profiles/weights_direct_N40962_n84.md); None until captured.
+WEIGHTS_DRAM_BYTES = None
 
 
 def weights_flops(m):
-    """Algorithmic FP64 flops of one augmented solve: LU of an m x m system with one
-    right-hand side ((2/3) m^3 for the elimination, 2 m^2 for the rhs and back substitution)."""
-    return 2.0 / 3.0 * m ** 3 + 2.0 * m ** 2
+    """Algorithmic FP64 flops of one saddle-point solve by symmetric indefinite factorisation
+    with one right-hand side: (1/3) m^3 for L D L^T (m^3 / 6 FMAs), 2 m^2 for the forward and
+    back substitutions."""
+    return 1.0 / 3.0 * m ** 3 + 2.0 * m ** 2
 
 
 def make_ctx(w, precision, stream, rbfsl, mode=None):
@@ -899,7 +900,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "weights_kernel<9, float2> (FP64 GEPP, look-ahead, m = 109)",
+        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 Bunch-Kaufman LDL^T, m = 109)",
                      "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": WEIGHTS_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",

@@ -136,11 +136,14 @@ int rbfsl_knn_query(const rbfsl_knn_index *index, const double *q, int64_t Nq, i
  *   [[A, P], [P^T, 0]] w~ = [phi(|p_i - x_Sj|)_j ; Y(p_i)],   w[i, :] = w~[0:n],
  * A_jk = phi(|x_Sj - x_Sk|), P_jc = Y_c(x_Sj), Y = real orthonormal spherical harmonics
  * of degree <= ell. Then the interpolant at p_i is sum_j w_ij f_Sj (the system is
- * symmetric). Gaussian elimination with partial pivoting, one warp per point.
+ * symmetric). Solved by a symmetric indefinite L D L^T factorisation with Bunch-Kaufman
+ * pivoting (1 x 1 and 2 x 2 pivots), one warp per point for small systems, four warps for
+ * larger ones; the result does not depend on that choice.
  *   x: device N x 3; idx: device Nq x n; p: device Nq x 3; w: device Nq x n of w_dtype
  *   (RBFSL_F64, RBFSL_F32 or RBFSL_F32X2: FP64 solve, result rounded or split into an FP32
  *   pair). status: device Nq or NULL
- *   (RBFSL_ESINGULAR for a zero pivot; w row NaN).
+ *   (RBFSL_ESINGULAR for two coincident stencil nodes or a zero or non-finite pivot; w row
+ *   NaN).
  * Errors: EINVAL (n < 1, ell > RBFSL_MAX_SH_DEGREE, n + (ell+1)^2 > RBFSL_MAX_SYSTEM,
  *   kernel not RBFSL_PHS with odd p >= 1), ECUDA. */
 int rbfsl_stencil_weights(const double *x, int64_t N, const int32_t *idx, int64_t Nq, int n,

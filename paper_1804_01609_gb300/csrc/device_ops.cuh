@@ -355,270 +355,6 @@ __host__ __device__ inline int knn_cap(int k) {
     while (cap < 3 * k) cap <<= 1;
     return cap;
 }
-// Trailing update of step k, flattened: rows times the columns j0..m form one index space that
-// the lanes walk in 32-element chunks, so that only a step's last chunk has idle lanes (an idle
-// lane of a DFMA still costs FP64 pipe time). kInterleave: the space is all remaining rows (list
-// positions k+1..m-1) and the NT warps take its chunks in turn (warp wi: chunks wi, wi + NT, ...;
-// shares equal to a chunk); otherwise warp wi's space is its own rows, positions k+1+wi, step NT
-// (shares equal to a row; measured better where a pivot warp shares an SM sub-partition with two
-// of the update warps). Per element the multiplier, the pivot-row value and the element are
-// loaded from shared memory; two chunks are loaded before either is stored. One FMA per element:
-// A[r][j] -= A[r][k] * A[pivot][j]. With kList false the rows are in place (position = row,
-// pivot row k) and L is unused.
-template <bool kList, bool kInterleave>
-__device__ __forceinline__ void trailing_update_flat(double *__restrict__ A, int ld, int m, int k, int j0,
-                                                     const int *__restrict__ L, int wi, int NT, int lane) {
-    const int first = kInterleave ? k + 1 : k + 1 + wi, step = kInterleave ? 1 : NT;
-    if (first >= m) return;
-    const int R = (m - 1 - first) / step + 1, C = m - j0 + 1;
-    const int E = R * C;
-    const int stride = kInterleave ? kWarp * NT : kWarp;
-    int e = (kInterleave ? kWarp * wi : 0) + lane;
-    if (e - lane >= E) return;
-    const int prow = kList ? L[k] : k;
-    auto row_of = [&](int rr) {
-        const int pos = first + rr * step;
-        return kList ? L[pos] : pos;
-    };
-    const int q = stride / C, rem = stride - q * C;  // one chunk turn: q rows and rem columns
-    int rr = e / C, cc = e - (e / C) * C;
-    auto advance = [&](int &r_, int &c_) {
-        r_ += q;
-        c_ += rem;
-        if (c_ >= C) { c_ -= C; ++r_; }
-    };
-    for (; e - lane + stride < E; e += 2 * stride) {
-        // chunk e - lane (all lanes active) and the next one of this warp (lanes below E)
-        int r1 = rr, c1 = cc;
-        advance(r1, c1);
-        const bool act0 = e < E, act1 = e + stride < E;
-        const int a0 = act0 ? row_of(rr) * ld : 0, a1 = act1 ? row_of(r1) * ld : 0;
-        double l0 = 0.0, u0 = 0.0, v0 = 0.0, l1 = 0.0, u1 = 0.0, v1 = 0.0;
-        if (act0) {
-            l0 = A[a0 + k];
-            u0 = A[prow * ld + j0 + cc];
-            v0 = A[a0 + j0 + cc];
-        }
-        if (act1) {
-            l1 = A[a1 + k];
-            u1 = A[prow * ld + j0 + c1];
-            v1 = A[a1 + j0 + c1];
-        }
-        if (act0) A[a0 + j0 + cc] = fma(-l0, u0, v0);
-        if (act1) A[a1 + j0 + c1] = fma(-l1, u1, v1);
-        rr = r1;
-        cc = c1;
-        advance(rr, cc);
-    }
-    if (e - lane < E && e < E) {
-        const int a0 = row_of(rr) * ld;
-        A[a0 + j0 + cc] = fma(-A[a0 + k], A[prow * ld + j0 + cc], A[a0 + j0 + cc]);
-    }
-}
-
-// Pivot of column k by one warp, rows at positions k..m-1 of list cur: the largest |a_rk|
-// (integer compare of the magnitude bits), the smaller position on a tie. Writes the list with
-// positions k and the pivot's swapped to nxt[k..m-1], the inverse pivot to invp[k] and the
-// multipliers a_rk / a_pk to column k of the remaining rows; *flag = 2 for a zero, infinite or
-// NaN pivot.
-__device__ __forceinline__ void pivot_step(double *__restrict__ A, int ld, int m, int k, const int *__restrict__ cur,
-                                           int *__restrict__ nxt, double *__restrict__ invp, int *flag, int lane) {
-    long long best = -1;
-    int bpos = m;
-    for (int p = k + lane; p < m; p += kWarp) {
-        const long long v = __double_as_longlong(A[cur[p] * ld + k]) & 0x7fffffffffffffffLL;
-        if (v > best) { best = v; bpos = p; }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-        const int oi = __shfl_xor_sync(0xffffffffu, bpos, off);
-        if (ob > best || (ob == best && oi < bpos)) { best = ob; bpos = oi; }
-    }
-    if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
-        if (lane == 0) *flag = 2;
-        return;
-    }
-    for (int p = k + lane; p < m; p += kWarp) nxt[p] = p == k ? cur[bpos] : (p == bpos ? cur[k] : cur[p]);
-    __syncwarp();
-    const int prow = nxt[k];
-    double inv = 0.0;
-    if (lane == 0) {
-        inv = 1.0 / A[prow * ld + k];
-        invp[k] = inv;
-    }
-    inv = __shfl_sync(0xffffffffu, inv, 0);
-    for (int p = k + 1 + lane; p < m; p += kWarp) A[nxt[p] * ld + k] *= inv;
-}
-
-// Shared-memory layout of one point: A (m x ld, the augmented [A~ | b] system), the stencil
-// coordinates (3 x n; after assembly the solution buffer), the inverse pivots (m), a flag word
-// and two row lists of m ints (multi-warp elimination).
-__host__ __device__ inline int stencil_doubles(int n, int m, int ld) { return m * ld + 3 * n + 2 * m + 1; }
-
-// Weights of one point by a group of NW warps (thread t of the group, NW * 32 threads):
-// assemble [[A, P], [P^T, 0] | phi(|p - x_j|); Y(p)] (Eqs. rbf_poly, rbf_poly_linsys) in the
-// group's shared region A and eliminate with partial pivoting (largest magnitude, smaller row
-// on a tie). Returns RBFSL_OK with the solution w~ in column m of A (rows 0..m-1, valid for
-// warp 0 of the group), RBFSL_EKNN for a stencil index < 0, RBFSL_ESINGULAR for a zero or
-// non-finite pivot. Every thread of the group must call it; with NW > 1 the group is the block.
-template <int NW>
-__device__ __forceinline__ int weights_point(double *__restrict__ A, const double *__restrict__ X,
-                                             const int32_t *__restrict__ stencil, int n, int m,
-                                             int ld, int ell, int half, double px, double py,
-                                             double pz, int t) {
-    constexpr int GT = NW * kWarp;
-    const int warp = t >> 5, lane = t & 31;
-    const int M = m - n;
-    double *cx = A + (size_t)m * ld, *cy = cx + n, *cz = cy + n, *invp = cz + n;
-    int *flag = reinterpret_cast<int *>(invp + m);
-    auto gsync = [] {
-        if (NW == 1) __syncwarp(); else __syncthreads();
-    };
-    if (t == 0) *flag = 0;
-    gsync();
-    for (int j = t; j < n; j += GT) {
-        const int64_t s = stencil[j];
-        if (s < 0) { *flag = 1; continue; }  // a failed neighbour search leaves -1
-        cx[j] = X[3 * s];
-        cy[j] = X[3 * s + 1];
-        cz[j] = X[3 * s + 2];
-    }
-    gsync();
-    if (*flag) return RBFSL_EKNN;
-
-    // ---- assembly. RBF block: the n(n-1)/2 pairs j < k are folded into rows of n-1 pairs
-    // (row f and row n-1-f together) so that every thread has work.
-    const int P2 = n * (n - 1) / 2;
-    for (int p = t; p < P2; p += GT) {
-        const int f = p / (n - 1), e = p - f * (n - 1);
-        int r, c;
-        if (e < n - 1 - f) { r = f; c = f + 1 + e; } else { r = n - 1 - f; c = e + 1; }
-        const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
-        const double v = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
-        A[r * ld + c] = v;
-        A[c * ld + r] = v;
-    }
-    for (int j = t; j < n; j += GT) {
-        A[j * ld + j] = 0.0;
-        sh_eval(ell, cx[j], cy[j], cz[j], [&](int c, double v) {
-            A[j * ld + n + c] = v;
-            A[(n + c) * ld + j] = v;
-        });
-        const double dx = px - cx[j], dy = py - cy[j], dz = pz - cz[j];
-        A[j * ld + m] = phs_from_d2(dx * dx + dy * dy + dz * dz, half);
-    }
-    for (int e = t; e < M * M; e += GT) A[(n + e / M) * ld + n + e % M] = 0.0;
-    if (warp == 0) sh_eval_lanes(ell, px, py, pz, lane, [&](int c, double v) { A[(n + c) * ld + m] = v; });
-    gsync();
-
-    if constexpr (NW > 1 && NW % 4 == 1) {
-        // ---- Gaussian elimination with partial pivoting on [A~ | b], look-ahead form with a
-        // pivot warp. Rows stay in place; a row list gives the order that the row swaps would.
-        // While warps 1..NW-1 (a multiple of four: one per SM sub-partition) apply step k to the
-        // columns k+2..m, warp 0 applies it to column k+1, finds the pivot of step k+1 and forms
-        // its multipliers, so that the pivot search and the division run beside the DFMAs (one
-        // barrier per step). Every element receives the same FMAs, and the pivots are the same
-        // (ties to the smaller position), as with swapped rows.
-        constexpr int NT = NW - 1;
-        int *L0 = flag + 2, *L1 = L0 + m;
-        if (warp == 0) {
-            for (int p = lane; p < m; p += kWarp) L0[p] = p;
-            __syncwarp();
-            pivot_step(A, ld, m, 0, L0, L1, invp, flag, lane);
-        }
-        __syncthreads();
-        if (*flag) return RBFSL_ESINGULAR;
-        int *L = L1, *Ln = L0;
-        for (int k = 0; k < m; ++k) {
-            if (warp == 0 && k + 1 < m) {
-                const int prow = L[k];
-                const double u = A[prow * ld + k + 1];
-                for (int p = k + 1 + lane; p < m; p += kWarp) {
-                    const int r = L[p];
-                    A[r * ld + k + 1] = fma(-A[r * ld + k], u, A[r * ld + k + 1]);
-                }
-                for (int p = lane; p <= k; p += kWarp) Ln[p] = L[p];  // fixed pivot positions
-                __syncwarp();
-                pivot_step(A, ld, m, k + 1, L, Ln, invp, flag, lane);
-            }
-            if (warp > 0 && k + 2 <= m) trailing_update_flat<true, false>(A, ld, m, k, k + 2, L, warp - 1, NT, lane);
-            __syncthreads();
-            if (*flag) return RBFSL_ESINGULAR;
-            if (k + 1 < m) {
-                int *tmp = L;
-                L = Ln;
-                Ln = tmp;
-            }
-        }
-        if (warp != 0) return RBFSL_OK;
-        // ---- back substitution on the rhs column (warp 0), pivot rows in list order, the
-        // solution gathered in the (no longer needed) coordinate buffer, then stored in column m
-        double *xs = cx;
-        for (int r = m - 1; r >= 0; --r) {
-            const double xr = A[L[r] * ld + m] * invp[r];
-            __syncwarp();
-            if (lane == 0) xs[r] = xr;
-            for (int s2 = lane; s2 < r; s2 += kWarp) {
-                const int q = L[s2];
-                A[q * ld + m] = fma(-A[q * ld + r], xr, A[q * ld + m]);
-            }
-            __syncwarp();
-        }
-        for (int r = lane; r < m; r += kWarp) A[r * ld + m] = xs[r];
-        __syncwarp();
-        return RBFSL_OK;
-    } else {
-    // ---- Gaussian elimination with partial pivoting on [A~ | b] (one warp: rows swapped)
-    for (int k = 0; k < m; ++k) {
-        if (warp == 0) {
-            // pivot: largest |a_rk| (integer compare of the magnitude bits), smaller row on a tie
-            long long best = -1;
-            int bidx = m;
-            for (int r = k + lane; r < m; r += kWarp) {
-                const long long v = __double_as_longlong(A[r * ld + k]) & 0x7fffffffffffffffLL;
-                if (v > best) { best = v; bidx = r; }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
-                if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-            }
-            if (best <= 0 || best >= 0x7ff0000000000000LL) {  // zero, inf or NaN pivot
-                if (lane == 0) *flag = 2;
-            } else {
-                if (bidx != k) {
-                    for (int c = k + lane; c <= m; c += kWarp) {
-                        const double tmp = A[k * ld + c];
-                        A[k * ld + c] = A[bidx * ld + c];
-                        A[bidx * ld + c] = tmp;
-                    }
-                    __syncwarp();
-                }
-                const double inv = 1.0 / A[k * ld + k];
-                if (lane == 0) invp[k] = inv;
-                for (int r = k + 1 + lane; r < m; r += kWarp) A[r * ld + k] *= inv;
-            }
-        }
-        gsync();
-        if (*flag) return RBFSL_ESINGULAR;
-        // trailing update: rows k+1..m-1, columns k+1..m, flattened over the NW warps
-        trailing_update_flat<false, true>(A, ld, m, k, k + 1, nullptr, warp, NW, lane);
-        gsync();
-    }
-    if (warp != 0) return RBFSL_OK;
-    // ---- back substitution on the rhs column (warp 0), with the stored inverse pivots
-    for (int r = m - 1; r >= 0; --r) {
-        const double xr = A[r * ld + m] * invp[r];
-        __syncwarp();
-        if (lane == 0) A[r * ld + m] = xr;
-        for (int s = lane; s < r; s += kWarp) A[s * ld + m] = fma(-A[s * ld + r], xr, A[s * ld + m]);
-        __syncwarp();
-    }
-    return RBFSL_OK;
-    }
-}
 
 // ---- Weights by symmetric indefinite factorisation. The saddle-point matrix
 // A~ = [[A, P], [P^T, 0]] of Eq. rbf_poly_linsys is symmetric, so A~ w~ = b is solved by
