@@ -131,8 +131,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
-# capture of this kernel version (profiles/weights_direct_N40962_n84.md); None until captured.
-WEIGHTS_DRAM_BYTES = None
+# capture of this kernel version (profiles/weights_direct_N40962_n84.md).
+WEIGHTS_DRAM_BYTES = 15.81e6
 
 
 def weights_flops(m):
