@@ -505,6 +505,43 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
     for ic in ("cosine", "gaussian"):
         mk = lambda N, n, ic=ic: inputs.config_nl(N, ic=ic, n=n)
         out[f"nl_{ic}_bells"] = {"local_center": sweep(mk, "local", rbfsl.CENTER, (31, 84), Ns)}
+
+    # error measures against the stencil / patch size n at N = 40,962 (the paper's dissipation
+    # and dispersion plots), local centre stencils and RBF-PU (overlap a = 2.5)
+    nsw = {}
+    for case, mk in (("sbr_cosine_bell", lambda n, meth: inputs.config_sbr(
+                          40962, method=meth, n=n, **({"ell": 3, "power": 7} if meth == "pu" and n >= 49 else {}))),
+                     ("nl_cosine_bells", lambda n, meth: inputs.config_nl(40962, ic="cosine", method=meth, n=n))):
+        nsw[case] = {meth: [dict(run(mk(n, meth), meth, rbfsl.CENTER if meth == "local" else None), n=n)
+                            for n in (17, 31, 49, 84)] for meth in ("local", "pu")}
+    out["n_sweep_N40962"] = nsw
+
+    # ten revolutions of the cosine bell with dt = pi/20 (the paper's mass-conservation run):
+    # mass error and l2 error after each revolution, N = 40,962, n = 49
+    def revolutions(method):
+        w = inputs.config_sbr(40962, method=method, n=49, steps=40, revolutions=10)
+        ctx = rbfsl.Context(0, stream=stream)
+        ctx.set_nodes(w.X)
+        ctx.set_velocity(w.vel_kind, w.vel_params)
+        ctx.set_integrator(rbfsl.RK5)
+        ctx.set_method(rbfsl.LOCAL if method == "local" else rbfsl.PU,
+                       rbfsl.CENTER if method == "local" else rbfsl.DIRECT)
+        ctx.set_stencil_size(w.n)
+        ctx.set_sh_degree(w.ell)
+        ctx.set_kernel(rbfsl.PHS, w.power)
+        if method == "pu":
+            ctx.set_pu(inputs.fibonacci_nodes(int(np.ceil(2.5 * w.N / w.n))))
+        ctx.set_dt(w.dt)
+        ctx.set_tracers(w.q0())
+        q0 = w.q0()[:, 0]
+        rows = []
+        for rev in range(1, 11):
+            ctx.step(40)
+            m = diagnostics.error_measures(ctx.get_q()[:, 0], q0)
+            rows.append({"revolution": rev, "l2": m["l2"], "mass": m["mass"]})
+        ctx.close()
+        return {"rows": rows, "l2_growth_10_over_1": rows[-1]["l2"] / rows[0]["l2"]}
+    out["sbr_ten_revolutions_N40962_n49"] = {"local": revolutions("local"), "pu": revolutions("pu")}
     return out
 
 
