@@ -193,9 +193,22 @@ int rbfsl_global_factor(const double *x, int64_t N, int kernel, double eps, doub
 int rbfsl_global_factor_noalloc(const double *x, int64_t N, int kernel, double eps, double *LU,
                                 int32_t *perm, void *stream);
 
+/* Cholesky factorisation of the same matrix (Sec. 3.3: the paper factorises its positive-
+ * definite IMQ matrix so), A_X = R^T R, blocked on the upper triangle (half the flops of
+ * elimination), returned in rbfsl_global_factor's form so that rbfsl_global_solve and
+ * rbfsl_global_cardinal take it unchanged: LU holds the unit lower L = R^T diag(R)^-1 below the
+ * diagonal and U = diag(R) R on and above it, perm the identity.
+ *   Arguments as rbfsl_global_factor. Allocates and frees O(N) device scratch, synchronises
+ *   `stream`. Errors: EINVAL, ENOMEM, ECUDA, ESINGULAR at a non-positive (or non-finite) pivot:
+ *   the matrix is not numerically positive definite (for example the Gaussian matrix at
+ *   eps = 6, N = 10,242) and LU holds no usable factor; the context then uses
+ *   rbfsl_global_factor. */
+int rbfsl_global_factor_chol(const double *x, int64_t N, int kernel, double eps, double *LU,
+                             int32_t *perm, void *stream);
+
 /* Coefficients of the global interpolant for T fields: solve A_X c = q with the factor of
- * rbfsl_global_factor (forward and backward substitution, FP64). q, c: device N x T, may not
- * alias. Errors: EINVAL, ECUDA. */
+ * rbfsl_global_factor or rbfsl_global_factor_chol (forward and backward substitution, FP64).
+ * q, c: device N x T, may not alias. Errors: EINVAL, ECUDA. */
 int rbfsl_global_solve(const double *LU, const int32_t *perm, int64_t N, const double *q, int T,
                        double *c, void *stream);
 
@@ -293,6 +306,8 @@ typedef struct rbfsl_stats {
     double time;               /* model time of the current field */
     size_t device_bytes;       /* device memory held by the context */
     int64_t device_timeouts;   /* nonzero if a bounded wait in a device kernel gave up */
+    int64_t global_cholesky;   /* global method: 1 if A_X was factorised by Cholesky, 0 if by
+                                  LU with partial pivoting (Cholesky broke down), -1 before */
 } rbfsl_stats;
 
 /* Create a context on `device` whose work is enqueued on `stream` (a cudaStream_t of that

@@ -91,6 +91,7 @@ struct rbfsl_ctx {
     size_t tc_ws_bytes = 0;
     int32_t *dev_err = nullptr;  // RBFSL_ETIMEDOUT from a bounded device wait
     int32_t *perm = nullptr, *piv = nullptr;
+    int global_cholesky = -1;  // global: 1 Cholesky, 0 LU (Cholesky broke down), -1 not factorised
     void *E = nullptr;         // global, cardinal form: Nq x N, FP64 or FP32 pairs
     void *card_ws = nullptr;   // its split-K partial sums
     size_t card_ws_bytes = 0;
@@ -154,6 +155,7 @@ void release_prepared(rbfsl_ctx *c) {
     c->tc_ws = nullptr; c->tc_ws_bytes = 0; c->dev_err = nullptr;
     cudaFree(c->E); cudaFree(c->card_ws);
     c->E = nullptr; c->card_ws = nullptr; c->card_ws_bytes = 0;
+    c->global_cholesky = -1;
     if (c->pu) rbfsl_pu_destroy(c->pu);
     c->pu = nullptr;
     c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
@@ -180,6 +182,21 @@ int effective_ell(const rbfsl_ctx *c) {
 // evaluation at the departure points.
 int prepare_global_cardinal(rbfsl_ctx *c);
 
+// A_X factorised by Cholesky as the paper does (Sec. 3.3); where that breaks down (a matrix
+// that is positive definite but not numerically so, e.g. Gaussian eps = 6 at N = 10,242) by LU
+// with partial pivoting. Both leave the factor in the form the solve takes.
+int factor_global(rbfsl_ctx *c) {
+    int rc = global_factor_chol_full(c->X, c->N, c->kkind, c->kparam, c->LU, c->perm, c->stream);
+    if (rc == RBFSL_OK) {
+        c->global_cholesky = 1;
+        return RBFSL_OK;
+    }
+    if (rc != RBFSL_ESINGULAR) return fail(c, rc, get_error());
+    CTX_RC(c, global_factor_full(c->X, c->N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
+    c->global_cholesky = 0;
+    return RBFSL_OK;
+}
+
 int prepare_global(rbfsl_ctx *c) {
     if (c->kkind != RBFSL_GAUSS && c->kkind != RBFSL_IMQ)
         return fail(c, RBFSL_EINVAL, "the global method needs RBFSL_GAUSS or RBFSL_IMQ");
@@ -201,7 +218,7 @@ int prepare_global(rbfsl_ctx *c) {
         c->tc_ws_bytes = global_eval_tc_workspace(N, N, (int)T);
         if ((rc = dalloc(c, &c->tc_ws, c->tc_ws_bytes))) return rc;
     }
-    CTX_RC(c, global_factor_full(c->X, N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
+    if ((rc = factor_global(c))) return rc;
     c->prepared_T = c->T;
     c->prepared = true;
     return RBFSL_OK;
@@ -226,7 +243,7 @@ int prepare_global_cardinal(rbfsl_ctx *c) {
     if (c->card_ws_bytes && (rc = dalloc(c, &c->card_ws, c->card_ws_bytes))) return rc;
     CTX_RC(c, launch_trace_order(c->X, N, c->vel_kind, c->vel, c->t + c->dt, c->dt, RBFSL_FP64, c->integrator,
                                  c->xi, c->stream));
-    CTX_RC(c, global_factor_full(c->X, N, c->kkind, c->kparam, c->LU, c->perm, c->piv, c->status, c->stream));
+    if ((rc = factor_global(c))) return rc;
     CTX_RC(c, global_cardinal_build(c->LU, c->perm, c->X, N, c->kkind, c->kparam, c->xi, N, c->E,
                                     c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2, c->stream));
     cudaFree(c->LU);
@@ -703,6 +720,7 @@ int rbfsl_get_stats(rbfsl_ctx *c, rbfsl_stats *out) {
     out->steps_done = c->steps_done;
     out->time = c->t;
     out->device_bytes = c->bytes;
+    out->global_cholesky = c->global_cholesky;
     return RBFSL_OK;
 }
 

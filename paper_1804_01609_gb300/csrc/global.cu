@@ -139,7 +139,9 @@ __global__ void lu_trsm_row(double *__restrict__ A, int64_t N, int64_t j0, int n
 // C[M x Nc] -= A[M x K] B[K x Nc], K <= 64, row-major with leading dimensions lda/ldb/ldc.
 // BM x BN output tiles, (BM/4)(BN/4) threads with 4 x 4 outputs each; K is staged through
 // shared memory in chunks of 32 (A transposed so that the inner-loop reads are conflict free).
-template <int BM, int BN>
+// kTransA: A is given transposed (Am[k * lda + row]); kUpper: only tiles that reach the
+// diagonal or above it are updated (the symmetric trailing update of the Cholesky factor).
+template <int BM, int BN, bool kTransA = false, bool kUpper = false>
 __global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_sub_f64(
     const double *__restrict__ Am, int64_t lda, const double *__restrict__ Bm, int64_t ldb,
     double *__restrict__ Cm, int64_t ldc, int64_t M, int64_t Nc, int K) {
@@ -147,14 +149,20 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_sub_f64(
     __shared__ double As[KC][BM + 1];  // As[k][row]
     __shared__ double Bs[KC][BN + 1];  // Bs[k][col]
     const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
+    if (kUpper && col0 + BN <= row0) return;  // every element of the tile below the diagonal
     const int t = threadIdx.x;
     const int tr = (t / (BN / 4)) * 4, tc = (t % (BN / 4)) * 4;
     double acc[4][4] = {};
     for (int k0 = 0; k0 < K; k0 += KC) {
         __syncthreads();
         for (int e = t; e < BM * KC; e += NT) {
-            const int r = e / KC, k = e % KC;
-            As[k][r] = (row0 + r < M && k0 + k < K) ? Am[(row0 + r) * lda + k0 + k] : 0.0;
+            if (kTransA) {
+                const int k = e / BM, r = e % BM;
+                As[k][r] = (row0 + r < M && k0 + k < K) ? Am[(k0 + k) * lda + row0 + r] : 0.0;
+            } else {
+                const int r = e / KC, k = e % KC;
+                As[k][r] = (row0 + r < M && k0 + k < K) ? Am[(row0 + r) * lda + k0 + k] : 0.0;
+            }
         }
         for (int e = t; e < KC * BN; e += NT) {
             const int kk = e / BN, c = e % BN;
@@ -252,6 +260,104 @@ int global_factor(double *A, int64_t N, int32_t *piv, int32_t *status, cudaStrea
         if (rc) return rc;
     }
     return RBFSL_OK;
+}
+
+// ---- Cholesky factorisation A_X = R^T R (Sec. 3.3: the paper's choice for its positive-definite
+// IMQ matrix), blocked right-looking on the upper triangle: the 64 x 64 diagonal block in one
+// CTA, the block row by triangular solves with R11^T, the trailing upper triangle by
+// R12^T R12 (tiles below the diagonal skipped: half of elimination's flops). status[0] is set
+// at a non-positive or non-finite pivot (breakdown; the caller falls back to LU).
+__global__ void __launch_bounds__(1024) chol_diag(double *__restrict__ A, int64_t N, int64_t j0, int nb,
+                                                  int32_t *__restrict__ status) {
+    __shared__ double D[kNb][kNb + 1];
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    if (t == 0) bad = 0;
+    for (int e = t; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = A[(j0 + e / nb) * N + j0 + e % nb];
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        if (t == 0) {
+            const double d = D[k][k];
+            if (!(d > 0.0) || !isfinite(d)) bad = 1;
+            D[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        const double r = D[k][k];
+        for (int c = k + 1 + t; c < nb; c += blockDim.x) D[k][c] /= r;
+        __syncthreads();
+        const int w = nb - k - 1;  // upper part of the remaining block: rows i, columns c >= i
+        for (int e = t; e < w * w; e += blockDim.x) {
+            const int i = k + 1 + e / w, c = k + 1 + e % w;
+            if (c >= i) D[i][c] = fma(-D[k][i], D[k][c], D[i][c]);
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, c = e % nb;
+        if (c >= i) A[(j0 + i) * N + j0 + c] = D[i][c];
+    }
+    if (t == 0 && bad) status[0] = RBFSL_ESINGULAR;
+}
+
+// R12 = R11^-T A12 for the block row j0..j0+nb, columns >= j0 + nb: thread per column.
+__global__ void chol_trsm_row(double *__restrict__ A, int64_t N, int64_t j0, int nb) {
+    __shared__ double R[kNb][kNb + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x)
+        R[e / nb][e % nb] = A[(j0 + e / nb) * N + j0 + e % nb];
+    __syncthreads();
+    const int64_t c = j0 + nb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double col[kNb];
+#pragma unroll
+    for (int r = 0; r < kNb; ++r) col[r] = r < nb ? A[(j0 + r) * N + c] : 0.0;
+#pragma unroll
+    for (int r = 0; r < kNb; ++r) {
+        if (r >= nb) break;
+        double s = col[r];
+#pragma unroll
+        for (int q = 0; q < r; ++q) s = fma(-R[q][r], col[q], s);
+        col[r] = s / R[r][r];
+    }
+#pragma unroll
+    for (int r = 0; r < kNb; ++r)
+        if (r < nb) A[(j0 + r) * N + c] = col[r];
+}
+
+// The factor in the elimination's form: L = R^T diag(R)^-1 below the diagonal (unit), U =
+// diag(R) R on and above it, so that the per-step solve takes it unchanged (identity row order).
+__global__ void chol_to_lu_lower(double *__restrict__ A, int64_t N, double *__restrict__ dg) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int64_t r = e / N, c = e - r * N;
+    if (r == c) dg[r] = A[e];
+    else if (r > c) A[e] = A[c * N + r] / A[c * N + c];
+}
+__global__ void chol_to_lu_upper(double *__restrict__ A, int64_t N, const double *__restrict__ dg) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N * N) return;
+    const int64_t r = e / N, c = e - r * N;
+    if (c >= r) A[e] = dg[r] * A[e];
+}
+
+int global_factor_chol(double *A, int64_t N, double *dg, int32_t *status, cudaStream_t s) {
+    for (int64_t j0 = 0; j0 < N; j0 += kNb) {
+        const int nb = (int)std::min<int64_t>(kNb, N - j0);
+        chol_diag<<<1, 1024, 0, s>>>(A, N, j0, nb, status);
+        const int64_t rest = N - j0 - nb;
+        if (rest > 0) {
+            chol_trsm_row<<<(unsigned)((rest + 127) / 128), 128, 0, s>>>(A, N, j0, nb);
+            const double *R12 = A + j0 * N + j0 + nb;
+            double *A22 = A + (j0 + nb) * N + j0 + nb;
+            dim3 grid((unsigned)((rest + 63) / 64), (unsigned)((rest + 63) / 64));
+            gemm_sub_f64<64, 64, true, true><<<grid, 256, 0, s>>>(R12, N, R12, N, A22, N, rest, rest, nb);
+        }
+        int rc = launch_status("global_factor_chol");
+        if (rc) return rc;
+    }
+    const int64_t NN = N * N;
+    chol_to_lu_lower<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(A, N, dg);
+    chol_to_lu_upper<<<(unsigned)((NN + 255) / 256), 256, 0, s>>>(A, N, dg);
+    return launch_status("global_factor_chol");
 }
 
 // ---- per-step solve C = A_X^-1 Q with the factor (row-major, T columns)
@@ -495,6 +601,53 @@ extern "C" int rbfsl_global_factor(const double *x, int64_t N, int kernel, doubl
     cudaFree(piv);
     cudaFree(status);
     return rc;
+}
+
+namespace rbfsl {
+// Assemble and factorise by Cholesky into the elimination's form (perm = identity). Returns
+// RBFSL_ESINGULAR at a breakdown (LU then holds no usable factor). Synchronises the stream.
+int global_factor_chol_full(const double *x, int64_t N, int kernel, double eps, double *LU, int32_t *perm,
+                            cudaStream_t s) {
+    double *dg = nullptr;
+    int32_t *status = nullptr;
+    if (cudaMalloc(&dg, N * sizeof(double)) != cudaSuccess || cudaMalloc(&status, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dg);
+        set_error("global_factor_chol: out of device memory");
+        return RBFSL_ENOMEM;
+    }
+    int rc = RBFSL_OK;
+    int32_t hs = 0;
+    std::vector<int32_t> id(N);
+    for (int64_t i = 0; i < N; ++i) id[i] = (int32_t)i;
+    if (cudaMemsetAsync(status, 0, sizeof(int32_t), s) != cudaSuccess) rc = RBFSL_ECUDA;
+    if (rc == RBFSL_OK) rc = launch_global_assemble(x, N, kernel, eps, LU, s);
+    if (rc == RBFSL_OK) rc = global_factor_chol(LU, N, dg, status, s);
+    if (rc == RBFSL_OK &&
+        (cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(perm, id.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess)) {
+        set_error(std::string("global_factor_chol: ") + cudaGetErrorString(cudaGetLastError()));
+        rc = RBFSL_ECUDA;
+    }
+    cudaFree(dg);
+    cudaFree(status);
+    if (rc == RBFSL_OK && hs != 0) {
+        set_error("global_factor_chol: non-positive pivot (the matrix is not numerically positive definite)");
+        rc = RBFSL_ESINGULAR;
+    }
+    return rc;
+}
+}  // namespace rbfsl
+
+extern "C" int rbfsl_global_factor_chol(const double *x, int64_t N, int kernel, double eps, double *LU,
+                                        int32_t *perm, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(N >= 1 && N <= 200000, "global_factor_chol: N out of range");
+    RBFSL_CHECK_ARG(x && LU && perm, "global_factor_chol: null pointer");
+    RBFSL_CHECK_ARG((kernel == RBFSL_GAUSS || kernel == RBFSL_IMQ) && eps > 0,
+                    "global_factor_chol: kernel must be RBFSL_GAUSS or RBFSL_IMQ with eps > 0");
+    return global_factor_chol_full(x, N, kernel, eps, LU, perm, (cudaStream_t)stream);
 }
 
 extern "C" int rbfsl_global_solve(const double *LU, const int32_t *perm, int64_t N, const double *q,

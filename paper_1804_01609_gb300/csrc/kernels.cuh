@@ -103,6 +103,8 @@ int launch_center_weights(const double *X, const int32_t *K, const int32_t *Ik, 
 
 int global_factor_full(const double *x, int64_t N, int kernel, double eps, double *LU, int32_t *perm,
                        int32_t *piv, int32_t *status, cudaStream_t s);
+int global_factor_chol_full(const double *x, int64_t N, int kernel, double eps, double *LU, int32_t *perm,
+                            cudaStream_t s);
 int global_solve(const double *LU, const int32_t *perm, int64_t N, const double *Q, int T,
                  double *C, cudaStream_t s);
 int launch_global_eval(const double *P, int64_t Nq, const double *X, int64_t N, int kind,

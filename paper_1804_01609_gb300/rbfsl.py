@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int64), ("singular_points", ctypes.c_int64),
                 ("knn_failures", ctypes.c_int64), ("uncovered_points", ctypes.c_int64),
                 ("time", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("device_timeouts", ctypes.c_int64)]
+                ("device_timeouts", ctypes.c_int64), ("global_cholesky", ctypes.c_int64)]
 
 
 SIGNATURES = {
@@ -66,6 +66,7 @@ SIGNATURES = {
     "rbfsl_gather_dot": (_I, [_P, _P, _I64, _I, _P, _I, _I, _P, _P]),
     "rbfsl_global_factor": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_factor_noalloc": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
+    "rbfsl_global_factor_chol": (_I, [_P, _I64, _I, _D, _P, _P, _P]),
     "rbfsl_global_solve": (_I, [_P, _P, _I64, _P, _I, _P, _P]),
     "rbfsl_global_eval": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _I, _P, _P]),
     "rbfsl_global_eval_tc_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
@@ -249,6 +250,12 @@ def rbfsl_global_factor_noalloc(x, kernel, eps, LU, perm, stream=None):
     """rbfsl_global_factor without any device allocation (scratch in a library-owned array)."""
     _check(load().rbfsl_global_factor_noalloc(_ptr(x), x.shape[0], kernel, float(eps), _ptr(LU),
                                               _ptr(perm), _stream(stream)))
+
+
+def rbfsl_global_factor_chol(x, kernel, eps, LU, perm, stream=None):
+    """Cholesky factor of A_X in rbfsl_global_factor's form (raises ESINGULAR on breakdown)."""
+    _check(load().rbfsl_global_factor_chol(_ptr(x), x.shape[0], kernel, float(eps), _ptr(LU), _ptr(perm),
+                                           _stream(stream)))
 
 
 def rbfsl_global_solve(LU, perm, q, c, stream=None):

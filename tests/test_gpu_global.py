@@ -121,3 +121,74 @@ def test_global_ctx_matches_oracle_small(orc):
     assert orc.rel_l2(q, ref) < 1e-9
     qm = _ctx(w, rbfsl.MIXED, w.steps)
     assert orc.rel_l2(qm, ref) < 1e-3
+
+
+@pytest.mark.parametrize("N,kernel,eps", [(642, rbfsl.IMQ, 4.0), (1000, rbfsl.IMQ, 4.0), (2562, rbfsl.GAUSS, 6.0)])
+def test_cholesky_factor_matches_oracle(orc, N, kernel, eps):
+    """rbfsl_global_factor_chol (Sec. 3.3): the factor R of A_X = R^T R against the oracle's
+    Cholesky factor to the perturbation bound ~cond(A_X) eps |R|; the returned L U form
+    reproduces A_X to Cholesky's backward-error bound (N+1) eps max_i a_ii (x4 for the
+    conversion to L U), has the identity row order, and solves through rbfsl_global_solve to
+    the LU residual bound. Panels of 64: N = 1000 leaves a ragged last panel."""
+    X = inputs.nodes(N, 5)
+    LU = torch.empty((N, N), dtype=torch.float64, device=DEV)
+    perm = torch.empty(N, dtype=torch.int32, device=DEV)
+    rbfsl.rbfsl_global_factor_chol(_t(X), kernel, eps, LU, perm)
+    F = LU.cpu().numpy()
+    assert (perm.cpu().numpy() == np.arange(N)).all()
+    U = np.triu(F)
+    dg = np.sqrt(np.diag(U))
+    R = U / dg[:, None]
+    A = orc.global_matrix(X, kernel, eps)
+    Lor = orc.cholesky(A)
+    assert Lor is not None
+    ep = np.finfo(float).eps
+    assert np.abs(R - Lor.T).max() <= 20 * np.linalg.cond(A) * ep * np.abs(Lor).max()
+    L = np.tril(F, -1) + np.eye(N)
+    assert np.abs(L @ U - A).max() <= 4 * (N + 1) * ep * np.diag(A).max()
+    Q = inputs.config_global_rotation(N=N, T=3).tracers(X)
+    C = torch.empty((N, 3), dtype=torch.float64, device=DEV)
+    rbfsl.rbfsl_global_solve(LU, perm, _t(Q), C)
+    Cn = C.cpu().numpy()
+    assert np.abs(A @ Cn - Q).max() <= lu_residual_bound(N, np.abs(A).sum(1).max(), Cn)
+
+
+def test_cholesky_breakdown_and_the_contexts_choice(orc):
+    """The workload's Gaussian matrix (eps = 6, N = 10,242) is not numerically positive
+    definite: rbfsl_global_factor_chol reports ESINGULAR and the context factorises by LU; the
+    IMQ matrix at N = 642 takes Cholesky, and the run matches the oracle's."""
+    w = inputs.config_global_rotation()
+    LU = torch.empty((w.N, w.N), dtype=torch.float64, device=DEV)
+    perm = torch.empty(w.N, dtype=torch.int32, device=DEV)
+    with pytest.raises(rbfsl.RbfslError) as e:
+        rbfsl.rbfsl_global_factor_chol(_t(w.X), rbfsl.GAUSS, w.eps, LU, perm)
+    assert e.value.code == rbfsl.ESINGULAR
+    del LU
+    ctx = rbfsl.Context(0)
+    ctx.set_nodes(w.X)
+    ctx.set_velocity(w.vel_kind, w.vel_params)
+    ctx.set_method(rbfsl.GLOBAL, rbfsl.DIRECT)
+    ctx.set_kernel(rbfsl.GAUSS, w.eps)
+    ctx.set_dt(w.dt)
+    ctx.set_tracers(w.q0()[:, :2])
+    assert ctx.get_stats().global_cholesky == -1
+    ctx.step(1)
+    assert ctx.get_stats().global_cholesky == 0
+    ctx.close()
+    s = inputs.config_global_rotation(N=642, T=3, steps=6)
+    ctx = rbfsl.Context(0)
+    ctx.set_nodes(s.X)
+    ctx.set_velocity(s.vel_kind, s.vel_params)
+    ctx.set_method(rbfsl.GLOBAL, rbfsl.DIRECT)
+    ctx.set_kernel(rbfsl.IMQ, 4.0)
+    ctx.set_dt(s.dt)
+    ctx.set_tracers(s.q0())
+    ctx.step(s.steps)
+    assert ctx.get_stats().global_cholesky == 1
+    q = ctx.get_q()
+    ctx.close()
+    G = orc.GlobalInterpolator(s.X, orc.IMQ, 4.0)
+    ref = s.q0()
+    for m in range(s.steps):
+        ref = G.apply(orc.trace_rk4(s.X, s.vel_kind, s.vel_params, (m + 1) * s.dt, s.dt), ref)
+    assert orc.rel_l2(q, ref) < 1e-9
