@@ -123,13 +123,15 @@ def test_global_ctx_matches_oracle_small(orc):
     assert orc.rel_l2(qm, ref) < 1e-3
 
 
-@pytest.mark.parametrize("N,kernel,eps", [(642, rbfsl.IMQ, 4.0), (1000, rbfsl.IMQ, 4.0), (2562, rbfsl.GAUSS, 6.0)])
+@pytest.mark.parametrize("N,kernel,eps", [(17, rbfsl.IMQ, 2.0), (642, rbfsl.IMQ, 4.0), (1000, rbfsl.IMQ, 4.0),
+                                         (2562, rbfsl.GAUSS, 6.0)])
 def test_cholesky_factor_matches_oracle(orc, N, kernel, eps):
     """rbfsl_global_factor_chol (Sec. 3.3): the factor R of A_X = R^T R against the oracle's
     Cholesky factor to the perturbation bound ~cond(A_X) eps |R|; the returned L U form
     reproduces A_X to Cholesky's backward-error bound (N+1) eps max_i a_ii (x4 for the
     conversion to L U), has the identity row order, and solves through rbfsl_global_solve to
-    the LU residual bound. Panels of 64: N = 1000 leaves a ragged last panel."""
+    the LU residual bound. Panels of 64: N = 1000 leaves a ragged last panel, N = 17 is one
+    partial panel."""
     X = inputs.nodes(N, 5)
     LU = torch.empty((N, N), dtype=torch.float64, device=DEV)
     perm = torch.empty(N, dtype=torch.int32, device=DEV)
