@@ -318,6 +318,10 @@ int rbfsl_destroy(rbfsl_ctx *ctx);
 /* Node set X (Sec. 3.1): N x 3 doubles on the host or the device, copied. Unit vectors
  * are expected (not checked). Invalidates prepared state. */
 int rbfsl_set_nodes(rbfsl_ctx *ctx, const double *xyz, int64_t N, int mem);
+/* Velocity field u (Sec. 3.2): kind RBFSL_VEL_* with its parameters (host, copied): 4 for
+ * RBFSL_VEL_RIGID (unit axis, angular speed), 2 for RBFSL_VEL_DEFORM_Y2 and RBFSL_VEL_NL
+ * (kappa, T_f > 0). With the cardinal global form selected it invalidates prepared state (the
+ * departure points change). Errors: EINVAL (kind, count, non-unit axis, T_f <= 0). */
 int rbfsl_set_velocity(rbfsl_ctx *ctx, int kind, const double *params, int nparams);
 int rbfsl_set_method(rbfsl_ctx *ctx, int method, int stencil_mode);
 /* Stencil size n (local) -- Sec. 2.2. */
