@@ -6,7 +6,8 @@ FP64 saddle-point weights, gather-dot W.q over all tracers): N = 40,962 Fibonacc
 (1e-3 rad jitter), stencils of n = 84 nearest nodes of each departure point, PHS r^9,
 spherical harmonics to degree 4, reversing deformational flow psi = 2.4 y^2 cos(pi t) over
 600 steps (T_f = 1), 32 tracers (one field of two Gaussian hills + 31 smooth random fields). Mixed
-precision = FP64 solves, FP32 tracing displacement and FP32 difference-form W.q.
+precision = FP64 solves, FP32 stage increments in the tracer, weights and fields as FP32 pairs
+with the W.q sum in pair arithmetic.
 
 The L2 cache (129 MB) is flushed between timed steps by writing a 256 MB buffer, so every
 step starts cold. Prints one JSON line (rank 0).
@@ -55,6 +56,24 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def job_seconds(local_seconds, world, device="cuda"):
+    """Wall time of the job's timed region: the maximum over the ranks of each rank's time
+    (one all-reduce; NCCL on the GPUs, gloo on the host)."""
+    if world <= 1:
+        return float(local_seconds)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job rate: the units every rank processed (replicas: world x one rank's) per
+    second of the job's wall time."""
+    return world * units_per_rank / seconds
 
 
 def workload():
@@ -802,12 +821,8 @@ def main():
     with ClockSampler(local) as clk:
         step_ms = timed_steps(ctx, args.steps, args.warmup, stream, flush, torch)
     barrier()
-    total_s = float(step_ms.sum()) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * N * args.steps / total_s
+    total_s = job_seconds(float(step_ms.sum()) / 1e3, world)
+    value = job_throughput(N * args.steps, world, total_s)
 
     # dominant kernel (FP64 stencil solve) and the gather-dot, timed alone on the same stream
     xi_t, I_t, _ = ctx.last_step_tensors(n, torch.float32)
