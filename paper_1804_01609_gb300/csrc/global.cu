@@ -1,13 +1,14 @@
 // Global RBF interpolation (Sec. 2.1, Eqs. srbfinterp and rbf_linsys; Sec. 3.3): the dense
-// N x N interpolation matrix A_X is factorised once (LU with partial pivoting, FP64), then
-// every step solves A_X C = Q for all tracers and evaluates the interpolant at the departure
-// points.
+// N x N interpolation matrix A_X is factorised once (Cholesky as in the paper, or LU with
+// partial pivoting where Cholesky breaks down; FP64), then every step solves A_X C = Q for all
+// tracers and evaluates the interpolant at the departure points.
 //
-// Storage is row-major FP64. The factorisation is blocked right-looking LU: per panel of 64
-// columns, a column-by-column pivot/scale/update, the row swaps applied to the rest of the
-// matrix, a unit-lower triangular solve for the panel's block row, and an FP64 tiled GEMM for
-// the trailing matrix. The per-step solve uses the same GEMM on 64-row blocks of the
-// triangular factors. All of it is bound by GB300's FP64 rate.
+// Storage is row-major FP64. LU is blocked right-looking: per panel of 64 columns, a
+// column-by-column pivot/scale/update, the row swaps applied to the rest of the matrix, a
+// unit-lower triangular solve for the panel's block row, and an FP64 tiled GEMM for the
+// trailing matrix. Cholesky is blocked on the upper triangle and handed on in LU form. The
+// per-step solve works on 64-row blocks of the triangular factors. All of it is bound by
+// GB300's FP64 rate.
 #include <algorithm>
 #include <cmath>
 #include <vector>
