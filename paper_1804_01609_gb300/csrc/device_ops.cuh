@@ -279,7 +279,10 @@ inline Vel<double> make_vel64(int kind, const double *prm) {
     return u;
 }
 
-__device__ __forceinline__ bool key_less(double da, int ia, double db, int ib) {
+// Order of the k-NN keys (d^2, index). Squared distances are non-negative (and the padding is
+// +infinity), and for such doubles the IEEE bit patterns read as 64-bit integers order exactly as
+// the values, so the comparison runs on the integer units instead of the FP64 pipe.
+__device__ __forceinline__ bool key_less(long long da, int ia, long long db, int ib) {
     return da < db || (da == db && ia < ib);
 }
 
@@ -291,15 +294,17 @@ __device__ __forceinline__ bool knn_warp(const KnnGrid &g, double qx, double qy,
                                          int cap, double *bd, int *bi, int *cnt, int lane) {
     double r2 = g.r2_per_k * k;
     const double target = 1.3 * k;
+    long long r2b;  // r2 as key bits
     int total = 0;
     bool ok = false;
     for (int iter = 0; iter < 40; ++iter) {
         if (lane == 0) *cnt = 0;
         __syncwarp();
         const double rb = sqrt(r2) * (1.0 + 1e-9) + 1e-15;
+        r2b = __double_as_longlong(r2);
         grid_ball_foreach(g, qx, qy, qz, rb, lane, [&](int p) {
             const double d2 = sqdist_rn(qx, qy, qz, g.sx[p], g.sy[p], g.sz[p]);
-            if (d2 <= r2) {
+            if (__double_as_longlong(d2) <= r2b) {  // d2 <= r2, both non-negative
                 const int slot = atomicAdd(cnt, 1);
                 if (slot < cap) {
                     bd[slot] = d2;
@@ -338,7 +343,7 @@ __device__ __forceinline__ bool knn_warp(const KnnGrid &g, double qx, double qy,
                     const bool up = (i & len) == 0;
                     const double di = bd[i], dj = bd[j];
                     const int ii = bi[i], ij = bi[j];
-                    if (key_less(dj, ij, di, ii) == up) {
+                    if (key_less(__double_as_longlong(dj), ij, __double_as_longlong(di), ii) == up) {
                         bd[i] = dj; bi[i] = ij;
                         bd[j] = di; bi[j] = ii;
                     }
