@@ -185,7 +185,9 @@ int rbfsl_global_factor(const double *x, int64_t N, int kernel, double eps, doub
  *   array of RBFSL_NOALLOC_FACTOR_MAX_N + 1 int32 that every GPU loading the library holds
  *   until exit; N above RBFSL_NOALLOC_FACTOR_MAX_N is rejected with EINVAL.
  *   Runs on the current device. The first call on a device looks up the array's device
- *   address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   address (cudaGetSymbolAddress); make that first call before any stream capture. The
+ *   address is kept for the life of the process: do not reset the device (cudaDeviceReset,
+ *   or a reset of its primary context) between calls, which would leave it stale.
  *   All calls share the one array: calls whose work overlaps on the GPU (other streams,
  *   other host threads) race and must be serialised by the caller.
  *   Arguments, outputs and errors as rbfsl_global_factor; synchronises `stream`. */
@@ -239,7 +241,9 @@ int rbfsl_pu_destroy(rbfsl_pu *pu);
  *   out[i] = sum_l phi_l(p_i) s_l(p_i) / sum_l phi_l(p_i)   over patches containing p_i,
  * phi_l(x) = phi(|x - omega_l| / R), phi = Wendland C2 (1-r)^4 (4r+1) (RBFSL_PU_WENDLAND) or
  * the paper's cubic B-spline (Eq. bspline, RBFSL_PU_BSPLINE). dtype RBFSL_F64: FP64
- * evaluation; RBFSL_F32: FP32 evaluation, out FP32. The handle keeps a coefficient buffer
+ * evaluation; RBFSL_F32: FP32 evaluation, out FP32; RBFSL_F32X2: each term's factor formed in
+ * FP64, coefficients and sums as FP32 pairs (hi, lo) in pair arithmetic, out N x T pairs
+ * (~n 2^-48 relative rounding, against the patch sums' cancellation). The handle keeps a coefficient buffer
  * (reallocated when T changes), so calls on one handle must not overlap.
  * status: device Nq or NULL (RBFSL_EUNCOVERED for a point in no patch, RBFSL_EINVAL for a
  * point in more than 32 patches; out row NaN). Errors: EINVAL, ENOMEM, ECUDA. */

@@ -10,6 +10,7 @@
 // per-step solve works on 64-row blocks of the triangular factors. All of it is bound by
 // GB300's FP64 rate.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -691,8 +692,10 @@ constexpr int64_t kNoAllocMaxN = RBFSL_NOALLOC_FACTOR_MAX_N;
 static __device__ __align__(256) int32_t g_factor_scratch[kNoAllocMaxN + 1];
 
 // Device address of g_factor_scratch for each device, looked up on the first call made on
-// that device (the name of a __device__ array in host code is not a device address).
-static int32_t *g_factor_scratch_ptr[64] = {nullptr};
+// that device (the name of a __device__ array in host code is not a device address) and kept
+// for the life of the process. Atomic so that host threads making their first calls at the same
+// time do not race on the entry (they may both look it up; they store the same address).
+static std::atomic<int32_t *> g_factor_scratch_ptr[64];
 
 // Final row order from the recorded swaps (one thread: N <= kNoAllocMaxN).
 __global__ void noalloc_row_order(const int32_t *__restrict__ piv, int64_t N, int32_t *__restrict__ perm) {
@@ -720,12 +723,11 @@ extern "C" int rbfsl_global_factor_noalloc(const double *x, int64_t N, int kerne
     int dev = 0;
     RBFSL_CUDA_TRY(cudaGetDevice(&dev));
     RBFSL_CHECK_ARG(dev >= 0 && dev < 64, "global_factor_noalloc: device index >= 64");
-    if (!g_factor_scratch_ptr[dev]) {
-        int32_t *ptr = nullptr;
-        RBFSL_CUDA_TRY(cudaGetSymbolAddress((void **)&ptr, g_factor_scratch));
-        g_factor_scratch_ptr[dev] = ptr;
+    int32_t *piv = g_factor_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!piv) {
+        RBFSL_CUDA_TRY(cudaGetSymbolAddress((void **)&piv, g_factor_scratch));
+        g_factor_scratch_ptr[dev].store(piv, std::memory_order_release);
     }
-    int32_t *piv = g_factor_scratch_ptr[dev];
     int32_t *status = piv + kNoAllocMaxN;
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: the status word must start at zero

@@ -65,3 +65,21 @@ def test_noalloc_factor_rejects_sizes_beyond_its_scratch():
     with pytest.raises(rbfsl.RbfslError) as e:
         rbfsl.rbfsl_global_factor_noalloc(x, rbfsl.GAUSS, EPS, LU, perm)
     assert e.value.code == rbfsl.EINVAL and "RBFSL_NOALLOC_FACTOR_MAX_N" in str(e.value)
+
+
+def test_noalloc_factor_starts_clean_after_a_singular_call():
+    # N nodes at one point: every entry of A_X is 1, the first elimination step leaves exact
+    # zeros, and the next pivot is zero. The status word in the shared array then reads
+    # ESINGULAR; the following call must clear it and succeed.
+    N = 100
+    Xs = np.tile(np.array([[0.0, 0.0, 1.0]]), (N, 1))
+    for fn in (rbfsl.rbfsl_global_factor, rbfsl.rbfsl_global_factor_noalloc):
+        with pytest.raises(rbfsl.RbfslError) as e:
+            _factor(fn, Xs)
+        assert e.value.code == rbfsl.ESINGULAR
+    X = inputs.nodes(642, 7)
+    LU_ref, perm_ref = _factor(rbfsl.rbfsl_global_factor, X)
+    LU, perm = _factor(rbfsl.rbfsl_global_factor_noalloc, X)
+    np.testing.assert_array_equal(perm.cpu().numpy(), perm_ref.cpu().numpy())
+    a, b = LU.cpu().numpy(), LU_ref.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
