@@ -7,10 +7,8 @@
 //     [ P^T  0 ]      [ Y(p)           ]      P_jc = Y_c(x_j)
 // and solves it by a Bunch-Kaufman L D L^T factorisation (weights_point_ldl): ~m^3 / 3 flops
 // per point, half of Gaussian elimination's, bound by GB300's FP64 rate. Small systems take one
-// warp per point (four points per block); larger ones four (or eight) warps per point, several
+// warp per point (four points per block); larger ones four warps per point, several
 // points per SM so that one point's pivot decisions overlap the others' updates.
-#include <cstdlib>
-
 #include "common.cuh"
 #include "kernels.cuh"
 #include "device_ops.cuh"
@@ -62,7 +60,7 @@ struct WeightsArgs {
     int32_t *status;
 };
 
-// NW warps per point (1, 4 or 8). With NW = 1 a block holds blockDim/32 independent points and
+// NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW > 1 a block is one point and uses __syncthreads.
 template <int NW, typename WT>
 __global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
@@ -114,13 +112,8 @@ int launch_weights(const double *x, const int32_t *idx, int64_t Nq, int n, int e
     a.region_doubles = ldl_doubles(n, a.m);
     const int bytes = a.region_doubles * 8;
     if (bytes > kWeightsSmallBytes) {
-        // larger systems (m >~ 45): four warps per point (RBFSL_WEIGHTS_WARPS=8: eight), one
-        // point per block, as many blocks per SM as shared memory allows (four at m = 109)
-        static const int nw = [] {
-            const char *e = getenv("RBFSL_WEIGHTS_WARPS");
-            return (e && atoi(e) == 8) ? 8 : 4;
-        }();
-        if (nw == 8) return launch_weights_typed<8>(a, 1, w, w_dtype, s);
+        // larger systems (m >~ 45): four warps per point (one per SM sub-partition), one point
+        // per block, as many blocks per SM as shared memory allows (four at m = 109)
         return launch_weights_typed<4>(a, 1, w, w_dtype, s);
     }
     return launch_weights_typed<1>(a, 4, w, w_dtype, s);  // four independent points (warps) per block
