@@ -17,6 +17,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   gepp_solve         numpy.linalg.solve (LAPACK dgesv), pivot-order invariance
   stencil_weights    sum w = 1, exact reproduction of every spherical harmonic of degree
                      <= ell, w = e_k at a node, agreement with an mpmath 50-digit solve
+  stencil_weights_ld the same system in long double: agreement with an mpmath 50-digit
+                     solve (to the long double's precision times the condition number),
+                     sum w = 1 and harmonic reproduction, w = e_k at a node
   local_step         return of a smooth field after a full revolution within method error
   global_*           interpolation at the nodes, LAPACK solve, Cholesky vs numpy
   global_cardinal    identity at the nodes (cardinal property), E q equal to solve-then-evaluate,
@@ -79,6 +82,8 @@ def lib():
                 "orc_cholesky": (_I, [_P, _I64]),
                 "orc_kernel": (_D, [_I, _D, _D]),
                 "orc_stencil_weights": (_I, [_P, _P, _I, _I, _I, _D, _P, _P]),
+                "orc_long_double_digits": (_I, []),
+                "orc_stencil_weights_ld": (_I64, [_P, _P, _I64, _I, _I, _I, _P, _P]),
                 "orc_local_apply": (_I64, [_P, _I64, _I, _I, _I, _D, _I, _P, _I64, _P, _I, _P, _P, _P]),
                 "orc_global_matrix": (None, [_P, _I64, _I, _D, _P]),
                 "orc_global_eval": (None, [_P, _I64, _P, _I64, _I, _D, _P, _I, _P]),
@@ -213,6 +218,22 @@ def stencil_weights(X, I, L, kkind, kprm, xi):
     if rc != 0:
         raise np.linalg.LinAlgError("singular stencil")
     return w
+
+
+def long_double_digits():
+    """Significand bits of the C long double the referee computes in (113 = IEEE binary128)."""
+    return int(lib().orc_long_double_digits())
+
+
+def stencil_weights_ld(X, I, L, power, Xi):
+    """Referee weights: the PHS r^power stencil systems of Eq. rbf_poly_linsys for the stencils
+    I (Nq x n) at the points Xi (Nq x 3), assembled and solved by partial-pivoting elimination
+    in long double (see long_double_digits), rounded to FP64. NaN rows for singular systems."""
+    X = _f64(X); I = np.ascontiguousarray(I, dtype=np.int32); Xi = _f64(Xi)
+    Nq, n = I.shape
+    W = np.empty((Nq, n))
+    lib().orc_stencil_weights_ld(_ptr(X), _ptr(I), Nq, n, L, int(power), _ptr(Xi), _ptr(W))
+    return W
 
 
 def local_apply(X, Xi, q, n, L, kkind, kprm, mode=DIRECT, want_IW=False):

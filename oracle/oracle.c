@@ -18,6 +18,7 @@
  *  - Gaussian elimination with partial pivoting; a pivot tie goes to the smaller row index;
  *  - k-NN key (d^2, index) compared lexicographically.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -388,6 +389,121 @@ int orc_stencil_weights(const double *X, const int32_t *I, int n, int L, int kki
     for (int i = 0; i < n; ++i) w[i] = b[i];
     free(A); free(b); free(Y);
     return rc;
+}
+
+/* ------------------------------------------------------------------ extended-precision referee */
+/* The same stencil system (Eqs. rbf_poly and rbf_poly_linsys) assembled and solved in long double,
+ * as a referee for FP64 weights whose system is too ill-conditioned for FP64 to fix them
+ * (condition numbers near 1e18 at n = 84, ell = 4). The node coordinates are the FP64 inputs,
+ * converted exactly; the kernel r^p, the harmonics and Gaussian elimination with partial
+ * pivoting are the double-precision steps above written in long double. long double is IEEE
+ * binary128 (113-bit significand) on aarch64 Linux and x87 extended (64 bits) on x86-64:
+ * orc_long_double_digits reports which. PHS kernel only. */
+int orc_long_double_digits(void) { return LDBL_MANT_DIG; }
+
+static void sh_eval_ld(int L, const long double *x, long double *Y) {
+    long double cm = 1.0L, sm = 0.0L;
+    for (int m = 0; m <= L; ++m) {
+        if (m > 0) {
+            long double c2 = cm * x[0] - sm * x[1];
+            long double s2 = cm * x[1] + sm * x[0];
+            cm = c2; sm = s2;
+        }
+        long double qmm = 1.0L;
+        for (int i = 1; i <= m; ++i) qmm *= (long double)(2 * i - 1);
+        long double qlm2 = 0.0L, qlm1 = 0.0L;
+        for (int l = m; l <= L; ++l) {
+            long double qlm;
+            if (l == m) qlm = qmm;
+            else if (l == m + 1) qlm = (long double)(2 * m + 1) * x[2] * qmm;
+            else qlm = ((long double)(2 * l - 1) * x[2] * qlm1 - (long double)(l + m - 1) * qlm2) / (long double)(l - m);
+            long double ratio = 1.0L;
+            for (int i = l - m + 1; i <= l + m; ++i) ratio /= (long double)i;
+            long double nlm = sqrtl((2.0L * l + 1.0L) / (4.0L * acosl(-1.0L)) * ratio);
+            if (m == 0) {
+                Y[l * l + l] = nlm * qlm;
+            } else {
+                Y[l * l + l + m] = sqrtl(2.0L) * nlm * qlm * cm;
+                Y[l * l + l - m] = sqrtl(2.0L) * nlm * qlm * sm;
+            }
+            qlm2 = qlm1; qlm1 = qlm;
+        }
+    }
+}
+
+static long double phs_ld(int p, const long double *a, const long double *b) {
+    long double d2 = 0.0L;
+    for (int c = 0; c < 3; ++c) d2 += (a[c] - b[c]) * (a[c] - b[c]);
+    long double v = sqrtl(d2);
+    for (int i = 0; i < (p - 1) / 2; ++i) v *= d2;
+    return v;
+}
+
+/* Weights of Nq stencils: I (Nq x n), points Xi (Nq x 3), PHS power p; W (Nq x n) receives the
+ * long-double weights rounded to double. Returns the number of singular stencils (NaN rows). */
+int64_t orc_stencil_weights_ld(const double *X, const int32_t *I, int64_t Nq, int n, int L, int p,
+                               const double *Xi, double *W) {
+    const int M = (L + 1) * (L + 1), m = n + M;
+    int64_t nsing = 0;
+#pragma omp parallel reduction(+ : nsing)
+    {
+        long double *A = (long double *)malloc(sizeof(long double) * (size_t)m * m);
+        long double *b = (long double *)malloc(sizeof(long double) * (size_t)m);
+        long double *C = (long double *)malloc(sizeof(long double) * 3 * (size_t)(n + 1));
+        long double *Y = (long double *)malloc(sizeof(long double) * (size_t)M);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t s = 0; s < Nq; ++s) {
+            const int32_t *S = I + s * n;
+            for (int j = 0; j < n; ++j)
+                for (int c = 0; c < 3; ++c) C[3 * j + c] = (long double)X[3 * (int64_t)S[j] + c];
+            for (int c = 0; c < 3; ++c) C[3 * n + c] = (long double)Xi[3 * s + c];
+            memset(A, 0, sizeof(long double) * (size_t)m * m);
+            for (int i = 0; i < n; ++i) {
+                for (int j = 0; j < n; ++j) A[(size_t)i * m + j] = i == j ? 0.0L : phs_ld(p, C + 3 * i, C + 3 * j);
+                sh_eval_ld(L, C + 3 * i, Y);
+                for (int c = 0; c < M; ++c) {
+                    A[(size_t)i * m + n + c] = Y[c];
+                    A[(size_t)(n + c) * m + i] = Y[c];
+                }
+                b[i] = phs_ld(p, C + 3 * n, C + 3 * i);
+            }
+            sh_eval_ld(L, C + 3 * n, Y);
+            for (int c = 0; c < M; ++c) b[n + c] = Y[c];
+            int bad = 0;
+            for (int k = 0; k < m && !bad; ++k) {
+                int q = k;
+                long double best = fabsl(A[(size_t)k * m + k]);
+                for (int i = k + 1; i < m; ++i) {
+                    long double v = fabsl(A[(size_t)i * m + k]);
+                    if (v > best) { best = v; q = i; }
+                }
+                if (!(best > 0.0L) || !isfinite(best)) { bad = 1; break; }
+                if (q != k) {
+                    for (int j = 0; j < m; ++j) {
+                        long double t = A[(size_t)k * m + j]; A[(size_t)k * m + j] = A[(size_t)q * m + j]; A[(size_t)q * m + j] = t;
+                    }
+                    long double t = b[k]; b[k] = b[q]; b[q] = t;
+                }
+                long double piv = A[(size_t)k * m + k];
+                for (int i = k + 1; i < m; ++i) {
+                    long double l = A[(size_t)i * m + k] / piv;
+                    if (l == 0.0L) continue;
+                    for (int j = k + 1; j < m; ++j) A[(size_t)i * m + j] -= l * A[(size_t)k * m + j];
+                    b[i] -= l * b[k];
+                }
+            }
+            if (!bad)
+                for (int i = m - 1; i >= 0; --i) {
+                    long double t = b[i];
+                    for (int j = i + 1; j < m; ++j) t -= A[(size_t)i * m + j] * b[j];
+                    b[i] = t / A[(size_t)i * m + i];
+                }
+            for (int j = 0; j < n; ++j) W[s * n + j] = bad ? NAN : (double)b[j];
+            nsing += bad;
+        }
+        free(A); free(b); free(C); free(Y);
+    }
+    return nsing;
 }
 
 /* ------------------------------------------------------------------ one local SL step */

@@ -107,3 +107,25 @@ def test_pu_every_point_covered(orc):
     X, pu = _pu(orc)
     P = inputs.random_unit_vectors(2000, np.random.default_rng(7))
     assert np.isfinite(pu.apply(P, np.ones(len(X)))).all()
+
+
+def test_oracle_global_iteration_diverges_at_the_workloads_eps_h(orc):
+    """Gaussian eps = 3 on 2,562 nodes has the eps h of the global workload (eps = 6 on 10,242):
+    the interpolation matrix is numerically singular (smallest LU pivot ~1e-14), and the FP64
+    semi-Lagrangian iteration tracks the exact solution for a few steps, then amplifies its
+    rounding noise about tenfold per step (Sec. 2.1, 3.3). The GPU's runs do the same, so the
+    divergence is the method's at this conditioning, not a defect of either implementation."""
+    from paper_1804_01609_gb300 import inputs
+    w = inputs.config_global_rotation(N=2562, eps=3.0, T=2)
+    G = orc.GlobalInterpolator(w.X, orc.GAUSS, w.eps)
+    assert np.abs(np.diag(G.LU)).min() < 1e-12
+    Xi = orc.trace_rk4(w.X, w.vel_kind, w.vel_params, w.dt, w.dt)
+    q = w.q0()
+    errs = []
+    for s in range(25):
+        q = G.apply(Xi, q)
+        ex = w.tracers(orc.exact_departure(w.X, w.vel_kind, w.vel_params, 0.0, (s + 1) * w.dt))
+        errs.append(orc.rel_l2(q, ex))
+    assert max(errs[:3]) < 1e-7
+    assert errs[-1] > 1e3
+    assert errs[-1] > 1e6 * errs[4]

@@ -15,6 +15,8 @@ from scipy.special import sph_harm_y
 
 from paper_1804_01609_gb300 import inputs
 
+import _mp_referee
+
 PHS = 0
 
 
@@ -113,3 +115,36 @@ def test_weights_vs_40_digit_solve(orc):
         ref = np.array([float(v) for v in mpmath.lu_solve(A, b)[:n]])
         w = orc.stencil_weights(X, I[i], ell, PHS, float(p), xi)
         assert np.abs(w - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_long_double_referee_vs_50_digit_solve(orc):
+    """The long-double referee (stencil_weights_ld) against a 50-digit solve of the same
+    polynomial system with its harmonics from mpmath's Legendre functions (tests/_mp_referee.py):
+    within the long double's precision times the system's conditioning (1e7 allowed here); with
+    IEEE binary128 that is the final rounding to FP64."""
+    N, n, ell, p = 2562, 31, 2, 3
+    X, P = _setup(N, n, npts=3)
+    I = orc.knn(X, P, n)
+    W = orc.stencil_weights_ld(X, I, ell, p, P)
+    for i, xi in enumerate(P):
+        ref = _mp_referee.mp_weights(X[I[i]], xi, ell, p)
+        tol = max(2.0 ** -52, 1e7 * 2.0 ** -orc.long_double_digits())
+        assert np.abs(W[i] - ref).max() <= tol * np.abs(ref).max()
+        assert abs(W[i].sum() - 1.0) < 1e-15
+
+
+def test_long_double_referee_at_a_node_and_invariants(orc):
+    """w = e_k at the k-th stencil node; sum w = 1 and reproduction of every harmonic of
+    degree <= ell (scipy's harmonics) at the m = 71 size, to the long double's precision."""
+    N, n, ell, p = 10242, 55, 3, 7
+    X, P = _setup(N, n, npts=4)
+    I = orc.knn(X, P, n)
+    W = orc.stencil_weights_ld(X, I, ell, p, P)
+    for i, xi in enumerate(P):
+        assert abs(W[i].sum() - 1.0) < 1e-12
+        Ys = _real_sh_scipy(ell, X[I[i]])
+        np.testing.assert_allclose(W[i] @ Ys, _real_sh_scipy(ell, xi)[0], atol=1e-12 * np.abs(W[i]).sum())
+    Ik = I[:1]
+    Wk = orc.stencil_weights_ld(X, Ik, ell, p, X[Ik[0, 5]][None])
+    e = np.zeros(n); e[5] = 1.0
+    np.testing.assert_allclose(Wk[0], e, atol=1e-9)
