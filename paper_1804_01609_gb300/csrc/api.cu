@@ -86,7 +86,6 @@ struct rbfsl_ctx {
     unsigned long long *ctr = nullptr;  // [singular, knn failures]
     // prepared state (global method)
     double *LU = nullptr, *C64 = nullptr, *Q64 = nullptr;
-    float *C32 = nullptr;  // RBF-PU: FP32 evaluation (mixed)
     void *tc_ws = nullptr;     // global, mixed: tensor-core evaluation workspace
     size_t tc_ws_bytes = 0;
     int32_t *dev_err = nullptr;  // RBFSL_ETIMEDOUT from a bounded device wait
@@ -150,7 +149,7 @@ void release_prepared(rbfsl_ctx *c) {
     cudaFree(c->xi); cudaFree(c->I); cudaFree(c->K); cudaFree(c->Ik); cudaFree(c->status);
     cudaFree(c->W); cudaFree(c->ctr);
     c->xi = nullptr; c->I = c->K = c->Ik = c->status = nullptr; c->W = nullptr; c->ctr = nullptr;
-    cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->C32); cudaFree(c->perm); cudaFree(c->piv);
+    cudaFree(c->LU); cudaFree(c->C64); cudaFree(c->Q64); cudaFree(c->perm); cudaFree(c->piv);
     cudaFree(c->tc_ws); cudaFree(c->dev_err);
     c->tc_ws = nullptr; c->tc_ws_bytes = 0; c->dev_err = nullptr;
     cudaFree(c->E); cudaFree(c->card_ws);
@@ -158,7 +157,7 @@ void release_prepared(rbfsl_ctx *c) {
     c->global_cholesky = -1;
     if (c->pu) rbfsl_pu_destroy(c->pu);
     c->pu = nullptr;
-    c->LU = c->C64 = c->Q64 = nullptr; c->C32 = nullptr; c->perm = c->piv = nullptr;
+    c->LU = c->C64 = c->Q64 = nullptr; c->perm = c->piv = nullptr;
     c->prepared = false;
 }
 
@@ -307,7 +306,6 @@ int prepare_pu(rbfsl_ctx *c) {
     CTX_TRY(c, cudaMemsetAsync(c->ctr, 0, 3 * sizeof(unsigned long long), c->stream));
     if (c->precision == RBFSL_MIXED) {
         if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
-        if ((rc = dalloc(c, &c->C32, N * T * sizeof(float)))) return rc;
     }
     CTX_RC(c, rbfsl_pu_create(&c->pu, c->X, N, c->pu_centers, c->pu_Mp, R, ell, c->kkind, c->kparam, c->stream));
     c->bytes += c->pu->bytes;
@@ -326,13 +324,10 @@ int one_step_pu(rbfsl_ctx *c) {
         from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, c->Q64, NT);
         q64 = c->Q64;
     }
+    // mixed: FP64 coefficient solves, the blend in FP32-pair arithmetic straight into the pair field
     CTX_RC(c, rbfsl_pu_apply(c->pu, q64, c->T, c->xi, N, c->pu_wkind,
-                             c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32,
-                             c->precision == RBFSL_FP64 ? c->q_next : (void *)c->C32, c->status, c->stream));
-    if (c->precision == RBFSL_MIXED) {
-        to_pair_kernel<float><<<blocks, 256, 0, c->stream>>>(c->C32, (float2 *)c->q_next, NT);
-        CTX_RC(c, launch_status("RBF-PU step (mixed)"));
-    }
+                             c->precision == RBFSL_FP64 ? RBFSL_F64 : RBFSL_F32X2, c->q_next, c->status,
+                             c->stream));
     count_status<<<(unsigned)((N + 255) / 256), 256, 0, c->stream>>>(c->status, N, c->ctr);
     std::swap(c->q, c->q_next);
     c->t = t1;

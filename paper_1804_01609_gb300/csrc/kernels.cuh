@@ -29,8 +29,9 @@ struct rbfsl_pu {
     int32_t *perm = nullptr;     // row order of each factor, at mstart[l] + l * M
     rbfsl_knn_index *nodes_ix = nullptr, *centers_ix = nullptr;
     double *coef = nullptr;      // (mstart[Mp] + Mp M) x coef_T
-    float *coef32 = nullptr;
+    void *coef32 = nullptr;      // FP32 or FP32-pair copy of coef for the mixed evaluations
     int coef_T = 0;
+    int64_t coef_len = 0;        // values in coef
     int32_t *status = nullptr;
     size_t bytes = 0;
 };

@@ -220,10 +220,62 @@ __global__ void __launch_bounds__(128) pu_coef_kernel(const int64_t *__restrict_
     for (int e = t; e < m * T; e += 128) out[e] = Y[e];
 }
 
+// Per-point patch search of the blend (one warp): the patches whose caps contain p, ordered by
+// patch index (the blend's summation order), their distances |p - omega_l|, the harmonics Y(p)
+// and the sum of the PU weight function. Returns the patch count, or -1 after writing NaN to the
+// point's outputs (via `fail`) and its status: EINVAL when more than kPuMaxPatches patches
+// overlap, EUNCOVERED when none contains p.
+struct PuPointShared {
+    int pl[4][kPuMaxPatches];
+    double pd[4][kPuMaxPatches];
+    int sl[4][kPuMaxPatches];
+    double sd[4][kPuMaxPatches];
+    int cnt[4];
+    double Ys[4][(RBFSL_MAX_SH_DEGREE + 1) * (RBFSL_MAX_SH_DEGREE + 1)];
+};
+
+template <typename Fail>
+__device__ __forceinline__ int pu_point_patches(const KnnGrid &cg, double Rr, int wkind, int ell, double px,
+                                                double py, double pz, int warp, int lane, PuPointShared &sh,
+                                                double &wsum, int32_t *status, int64_t i, Fail fail) {
+    if (lane == 0) sh.cnt[warp] = 0;
+    __syncwarp();
+    grid_ball_foreach(cg, px, py, pz, Rr * (1.0 + 1e-9) + 1e-15, lane, [&](int p) {
+        const double d = sqrt(sqdist_rn(px, py, pz, cg.sx[p], cg.sy[p], cg.sz[p]));
+        if (d < Rr) {
+            const int slot = atomicAdd(&sh.cnt[warp], 1);
+            if (slot < kPuMaxPatches) { sh.pl[warp][slot] = cg.sid[p]; sh.pd[warp][slot] = d; }
+        }
+    });
+    __syncwarp();
+    if (sh.cnt[warp] > kPuMaxPatches) {  // more overlapping patches than the kernel gathers
+        fail();
+        if (status && lane == 0) status[i] = RBFSL_EINVAL;
+        return -1;
+    }
+    const int np = sh.cnt[warp];
+    if (lane < np) {
+        int rank = 0;
+        for (int j = 0; j < np; ++j) rank += sh.pl[warp][j] < sh.pl[warp][lane];
+        sh.sl[warp][rank] = sh.pl[warp][lane];
+        sh.sd[warp][rank] = sh.pd[warp][lane];
+    }
+    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { sh.Ys[warp][c] = v; });
+    __syncwarp();
+    wsum = 0.0;
+    for (int a = 0; a < np; ++a) wsum += pu_phi(wkind, sh.sd[warp][a] / Rr);
+    if (np == 0 || !(wsum > 0.0)) {
+        fail();
+        if (status && lane == 0) status[i] = RBFSL_EUNCOVERED;
+        return -1;
+    }
+    return np;
+}
+
 // Blend the patch interpolants at Nq points; one warp per point, tracers in chunks of 16.
+// R = double: FP64 throughout; R = float: FP32 kernel values and sums.
 template <typename R>
-__global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *__restrict__ Om,
-                                                      double Rr, int wkind,
+__global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, double Rr, int wkind,
                                                       const double *__restrict__ X,
                                                       const int64_t *__restrict__ mstart,
                                                       const int32_t *__restrict__ members, int M,
@@ -232,47 +284,16 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
                                                       int64_t Nq, R *__restrict__ out,
                                                       int32_t *__restrict__ status) {
     constexpr int TC = 16;
-    __shared__ int pl[4][kPuMaxPatches];
-    __shared__ double pd[4][kPuMaxPatches];
-    __shared__ int sl[4][kPuMaxPatches];
-    __shared__ double sd[4][kPuMaxPatches];
-    __shared__ int cnt[4];
-    __shared__ double Ys[4][(RBFSL_MAX_SH_DEGREE + 1) * (RBFSL_MAX_SH_DEGREE + 1)];
+    __shared__ PuPointShared sh;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 4 + warp;
     if (i >= Nq) return;
     const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
-    if (lane == 0) cnt[warp] = 0;
-    __syncwarp();
-    grid_ball_foreach(cg, px, py, pz, Rr * (1.0 + 1e-9) + 1e-15, lane, [&](int p) {
-        const double d = sqrt(sqdist_rn(px, py, pz, cg.sx[p], cg.sy[p], cg.sz[p]));
-        if (d < Rr) {
-            const int slot = atomicAdd(&cnt[warp], 1);
-            if (slot < kPuMaxPatches) { pl[warp][slot] = cg.sid[p]; pd[warp][slot] = d; }
-        }
+    double wsum;
+    const int np = pu_point_patches(cg, Rr, wkind, ell, px, py, pz, warp, lane, sh, wsum, status, i, [&] {
+        for (int c = lane; c < T; c += 32) out[i * T + c] = (R)NAN;
     });
-    __syncwarp();
-    if (cnt[warp] > kPuMaxPatches) {  // more overlapping patches than the kernel gathers
-        for (int c = lane; c < T; c += 32) out[i * T + c] = (R)NAN;
-        if (status && lane == 0) status[i] = RBFSL_EINVAL;
-        return;
-    }
-    const int np = cnt[warp];
-    if (lane < np) {  // order the patches by index (the blend's summation order)
-        int rank = 0;
-        for (int j = 0; j < np; ++j) rank += pl[warp][j] < pl[warp][lane];
-        sl[warp][rank] = pl[warp][lane];
-        sd[warp][rank] = pd[warp][lane];
-    }
-    if (lane == 0) sh_eval(ell, px, py, pz, [&](int c, double v) { Ys[warp][c] = v; });
-    __syncwarp();
-    double wsum = 0.0;
-    for (int a = 0; a < np; ++a) wsum += pu_phi(wkind, sd[warp][a] / Rr);
-    if (np == 0 || !(wsum > 0.0)) {
-        for (int c = lane; c < T; c += 32) out[i * T + c] = (R)NAN;
-        if (status && lane == 0) status[i] = RBFSL_EUNCOVERED;
-        return;
-    }
+    if (np < 0) return;
     const R winv = (R)(1.0 / wsum);
     for (int t0 = 0; t0 < T; t0 += TC) {
         const int tc = min(TC, T - t0);
@@ -280,8 +301,8 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
 #pragma unroll
         for (int c = 0; c < TC; ++c) acc[c] = R(0);
         for (int a = 0; a < np; ++a) {
-            const int64_t l = sl[warp][a];
-            const R wl = (R)pu_phi(wkind, sd[warp][a] / Rr) * winv;
+            const int64_t l = sh.sl[warp][a];
+            const R wl = (R)pu_phi(wkind, sh.sd[warp][a] / Rr) * winv;
             const int n = (int)(mstart[l + 1] - mstart[l]);
             const int32_t *I = members + mstart[l];
             const R *C = coef + (mstart[l] + l * M) * T + t0;
@@ -305,7 +326,7 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
                     if (c < tc) acc[c] = fma(f, C[(int64_t)j * T + c], acc[c]);
             }
             for (int k = lane; k < M; k += 32) {
-                const R yv = (R)Ys[warp][k] * wl;
+                const R yv = (R)sh.Ys[warp][k] * wl;
 #pragma unroll
                 for (int c = 0; c < TC; ++c)
                     if (c < tc) acc[c] = fma(yv, C[(int64_t)(n + k) * T + c], acc[c]);
@@ -316,6 +337,72 @@ __global__ void __launch_bounds__(128) pu_eval_kernel(KnnGrid cg, const double *
             R v = acc[c];
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
             if (lane == 0 && c < tc) out[i * T + t0 + c] = v;
+        }
+    }
+    if (status && lane == 0) status[i] = RBFSL_OK;
+}
+
+// The blend for the mixed step: each term's factor (kernel value or harmonic times the
+// normalised PU weight) is formed in FP64 as in the FP64 kernel and split into an FP32 pair;
+// coefficients are FP32 pairs; the sums are pair arithmetic with FP32 operations (pair_fma,
+// then a two-sum reduction over the lanes). The patch sums cancel strongly (sum |c phi| reaches
+// ~3e3 |s|), which plain FP32 sums turn into ~1e-4 relative errors; pairs keep ~n 2^-48.
+__global__ void __launch_bounds__(128) pu_eval_pair_kernel(KnnGrid cg, double Rr, int wkind,
+                                                           const double *__restrict__ X,
+                                                           const int64_t *__restrict__ mstart,
+                                                           const int32_t *__restrict__ members, int M,
+                                                           int ell, int half, const float2 *__restrict__ coef,
+                                                           int T, const double *__restrict__ P, int64_t Nq,
+                                                           float2 *__restrict__ out, int32_t *__restrict__ status) {
+    constexpr int TC = 16;
+    __shared__ PuPointShared sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 4 + warp;
+    if (i >= Nq) return;
+    const double px = P[3 * i], py = P[3 * i + 1], pz = P[3 * i + 2];
+    double wsum;
+    const int np = pu_point_patches(cg, Rr, wkind, ell, px, py, pz, warp, lane, sh, wsum, status, i, [&] {
+        for (int c = lane; c < T; c += 32) out[i * T + c] = make_float2(NAN, NAN);
+    });
+    if (np < 0) return;
+    const double winv = 1.0 / wsum;
+    for (int t0 = 0; t0 < T; t0 += TC) {
+        const int tc = min(TC, T - t0);
+        float ah[TC], al[TC];
+#pragma unroll
+        for (int c = 0; c < TC; ++c) ah[c] = al[c] = 0.f;
+        for (int a = 0; a < np; ++a) {
+            const int64_t l = sh.sl[warp][a];
+            const double wl = pu_phi(wkind, sh.sd[warp][a] / Rr) * winv;
+            const int n = (int)(mstart[l + 1] - mstart[l]);
+            const int32_t *I = members + mstart[l];
+            const float2 *C = coef + (mstart[l] + l * M) * T + t0;
+            for (int j = lane; j < n; j += 32) {
+                const int64_t s = I[j];
+                const double dx = px - X[3 * s], dy = py - X[3 * s + 1], dz = pz - X[3 * s + 2];
+                const float2 f = pair_from(phs_from_d2(dx * dx + dy * dy + dz * dz, half) * wl);
+#pragma unroll
+                for (int c = 0; c < TC; ++c)
+                    if (c < tc) pair_fma(f, C[(int64_t)j * T + c], ah[c], al[c]);
+            }
+            for (int k = lane; k < M; k += 32) {
+                const float2 yv = pair_from(sh.Ys[warp][k] * wl);
+#pragma unroll
+                for (int c = 0; c < TC; ++c)
+                    if (c < tc) pair_fma(yv, C[(int64_t)(n + k) * T + c], ah[c], al[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < TC; ++c) {
+            float h = ah[c], lo = al[c];
+            for (int off = 16; off > 0; off >>= 1) {  // pair sums across the lanes (two-sum)
+                const float oh = __shfl_xor_sync(0xffffffffu, h, off), ol = __shfl_xor_sync(0xffffffffu, lo, off);
+                const float s2 = h + oh, bp = s2 - h;
+                const float e = (h - (s2 - bp)) + (oh - bp);
+                lo = lo + (ol + e);
+                h = s2;
+            }
+            if (lane == 0 && c < tc) out[i * T + t0 + c] = pair_norm(h, lo);
         }
     }
     if (status && lane == 0) status[i] = RBFSL_OK;
@@ -335,6 +422,11 @@ int launch_stencil_factor(const double *X, const int64_t *mstart, const int32_t 
     pu_factor_kernel<<<(unsigned)count, 128, smem, s>>>(X, mstart, members, lu_off, M, ell, (power - 1) / 2,
                                                         LU, perm, status, colmajor);
     return launch_status("stencil_factor");
+}
+
+__global__ void pu_to_pairs(const double *__restrict__ in, float2 *__restrict__ out, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = pair_from(in[e]);
 }
 
 template <typename A, typename B>
@@ -436,12 +528,13 @@ int pu_apply(rbfsl_pu *u, const double *q, int T, const double *p, int64_t Nq, i
         RBFSL_CUDA_TRY(cudaMemcpy(&tot, u->mstart + u->Mp, sizeof(int64_t), cudaMemcpyDeviceToHost));
         tot = (tot + u->Mp * u->M) * T;
         if (cudaMalloc(&u->coef, tot * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&u->coef32, tot * sizeof(float)) != cudaSuccess) {
+            cudaMalloc(&u->coef32, tot * sizeof(float2)) != cudaSuccess) {
             cudaGetLastError();
             set_error("pu_apply: out of device memory");
             return RBFSL_ENOMEM;
         }
         u->coef_T = T;
+        u->coef_len = tot;
     }
     const int mmax = u->max_members + u->M;
     const int smem = mmax * T * (int)sizeof(double);
@@ -455,15 +548,18 @@ int pu_apply(rbfsl_pu *u, const double *q, int T, const double *p, int64_t Nq, i
     const KnnGrid cg = grid_view(u->centers_ix);
     const int half = (u->power - 1) / 2;
     if (dtype == RBFSL_F64) {
-        pu_eval_kernel<double><<<blocks, 128, 0, s>>>(cg, u->centers, u->R, wkind, u->X, u->mstart, u->members,
+        pu_eval_kernel<double><<<blocks, 128, 0, s>>>(cg, u->R, wkind, u->X, u->mstart, u->members,
                                                       u->M, u->ell, half, u->coef, T, p, Nq, (double *)out, status);
+    } else if (dtype == RBFSL_F32) {
+        pu_convert<double, float><<<(unsigned)((u->coef_len + 255) / 256), 256, 0, s>>>(u->coef, (float *)u->coef32,
+                                                                                       u->coef_len);
+        pu_eval_kernel<float><<<blocks, 128, 0, s>>>(cg, u->R, wkind, u->X, u->mstart, u->members,
+                                                     u->M, u->ell, half, (const float *)u->coef32, T, p, Nq,
+                                                     (float *)out, status);
     } else {
-        int64_t tot = 0;
-        RBFSL_CUDA_TRY(cudaMemcpy(&tot, u->mstart + u->Mp, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        tot = (tot + u->Mp * u->M) * T;
-        pu_convert<double, float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(u->coef, u->coef32, tot);
-        pu_eval_kernel<float><<<blocks, 128, 0, s>>>(cg, u->centers, u->R, wkind, u->X, u->mstart, u->members,
-                                                     u->M, u->ell, half, u->coef32, T, p, Nq, (float *)out, status);
+        pu_to_pairs<<<(unsigned)((u->coef_len + 255) / 256), 256, 0, s>>>(u->coef, (float2 *)u->coef32, u->coef_len);
+        pu_eval_pair_kernel<<<blocks, 128, 0, s>>>(cg, u->R, wkind, u->X, u->mstart, u->members, u->M, u->ell,
+                                                   half, (const float2 *)u->coef32, T, p, Nq, (float2 *)out, status);
     }
     return launch_status("pu_eval");
 }
@@ -508,7 +604,7 @@ extern "C" int rbfsl_pu_apply(rbfsl_pu *u, const double *q, int T, const double 
     RBFSL_CHECK_ARG(T >= 1 && Nq >= 0, "pu_apply: bad sizes");
     RBFSL_CHECK_ARG(q && (Nq == 0 || (p && out)), "pu_apply: null pointer");
     RBFSL_CHECK_ARG(weight_kind == RBFSL_PU_WENDLAND || weight_kind == RBFSL_PU_BSPLINE, "pu_apply: bad weight kind");
-    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32, "pu_apply: bad dtype");
+    RBFSL_CHECK_ARG(dtype == RBFSL_F64 || dtype == RBFSL_F32 || dtype == RBFSL_F32X2, "pu_apply: bad dtype");
     const int mmax = u->max_members + u->M;
     RBFSL_CHECK_ARG((size_t)mmax * T * sizeof(double) <= 200 * 1024, "pu_apply: too many tracers for one call");
     return pu_apply(u, q, T, p, Nq, weight_kind, dtype, out, status, (cudaStream_t)stream);

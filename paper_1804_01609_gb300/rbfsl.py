@@ -299,10 +299,17 @@ def rbfsl_pu_create(x, centers, radius, ell, kernel, kparam, stream=None) -> PUP
     return PUPatches(x, centers, radius, ell, kernel, kparam, stream)
 
 
-def rbfsl_pu_apply(pu, q, p, weight_kind, out, status=None, stream=None):
+def rbfsl_pu_apply(pu, q, p, weight_kind, out, status=None, stream=None, pairs=False):
+    """pairs=True: out holds FP32 pairs (Nq x T x 2 float32), the RBFSL_F32X2 evaluation."""
     T = q.shape[1] if q.dim() == 2 else 1
+    if pairs:
+        if out.dtype.itemsize != 4 or out.dim() != 3 or out.shape[2] != 2:
+            raise ValueError("pairs=True wants out of shape Nq x T x 2 (float32)")
+        code = F32X2
+    else:
+        code = _dtype_code(out)
     _check(load().rbfsl_pu_apply(pu.handle, _ptr(q), T, _ptr(p), p.shape[0], weight_kind,
-                                 _dtype_code(out), _ptr(out), _ptr(status), _stream(stream)))
+                                 code, _ptr(out), _ptr(status), _stream(stream)))
 
 
 class Problem(ctypes.Structure):

@@ -33,13 +33,15 @@ def _setup(N, n, ell=3, power=7, a=2.5, seed=4):
     return X, Om, R
 
 
-def _gpu_apply(X, Om, R, q, P, ell=3, power=7, wkind=0, dtype=torch.float64):
+def _gpu_apply(X, Om, R, q, P, ell=3, power=7, wkind=0, dtype=torch.float64, pairs=False):
     pu = rbfsl.rbfsl_pu_create(_t(X), _t(Om), R, ell, rbfsl.PHS, power)
     q2 = q.reshape(len(X), -1)
-    out = torch.empty((len(P), q2.shape[1]), dtype=dtype, device=DEV)
+    shape = (len(P), q2.shape[1], 2) if pairs else (len(P), q2.shape[1])
+    out = torch.empty(shape, dtype=torch.float32 if pairs else dtype, device=DEV)
     st = torch.full((len(P),), 99, dtype=torch.int32, device=DEV)
-    rbfsl.rbfsl_pu_apply(pu, _t(q2), _t(P), wkind, out, st)
-    res = out.cpu().numpy().astype(np.float64), st.cpu().numpy()
+    rbfsl.rbfsl_pu_apply(pu, _t(q2), _t(P), wkind, out, st, pairs=pairs)
+    o = out.cpu().numpy().astype(np.float64)
+    res = (o[..., 0] + o[..., 1] if pairs else o), st.cpu().numpy()
     pu.close()
     return res
 
@@ -133,3 +135,28 @@ def test_pu_full_size_sampled(orc):
     assert (st == 0).all()
     ref = orc.PUInterpolator(X, Om, n, 3, 7, R=R).apply(P, q)
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("wkind", [0, 1])
+def test_pu_pair_eval(orc, wkind):
+    """The mixed step's blend (RBFSL_F32X2: FP64 factors, FP32-pair sums) against the FP64
+    evaluation to 1e-10 of max|q| (pair rounding ~n 2^-48 times the patch sums' cancellation
+    of ~3e3), and against the oracle within 5 times its one-ulp noise floor plus that bound;
+    uncovered points give NaN pairs and EUNCOVERED."""
+    N, n = 2562, 60
+    X, Om, R = _setup(N, n)
+    P = inputs.random_unit_vectors(1000, np.random.default_rng(2))
+    q = inputs.config_local_deformation(N=N, n_random=3).tracers(X)
+    g64, _ = _gpu_apply(X, Om, R, q, P, wkind=wkind)
+    gp, st = _gpu_apply(X, Om, R, q, P, wkind=wkind, pairs=True)
+    assert (st == 0).all()
+    scale = np.abs(q).max()
+    assert np.abs(gp - g64).max() <= 1e-10 * scale
+    ref = orc.PUInterpolator(X, Om, n, 3, 7, weight_kind=wkind, R=R).apply(P, q)
+    s = np.random.default_rng(0).choice([-1.0, 1.0], size=X.shape)
+    alt = orc.PUInterpolator(np.nextafter(X, X + s), Om, n, 3, 7, weight_kind=wkind, R=R).apply(P, q)
+    floor = np.abs(alt - ref).max()
+    assert np.abs(gp - ref).max() <= 5 * floor + 1e-10 * scale
+    keep = Om[:, 2] > 0.2
+    out, st = _gpu_apply(X, Om[keep], R, q, np.array([[0.0, 0.0, -1.0]]), wkind=wkind, pairs=True)
+    assert st[0] == rbfsl.EUNCOVERED and np.isnan(out[0]).all()
