@@ -1,5 +1,6 @@
 """Batched local RBF-SL (many problems, one persistent fused kernel per step, CUDA graph):
-every problem's result must be bit-identical to the same problem stepped alone and to the
+every problem's result must match the oracle's run of the same problem (Algorithm 1; criteria
+in tests/_parity.py), and be bit-identical to the same problem stepped alone and to the
 single-problem context path, with or without the graph, before and after autotuning, and
 while other problems are added and removed."""
 import numpy as np
@@ -8,6 +9,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_1804_01609_gb300 import inputs, rbfsl  # noqa: E402
+
+import _parity  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -30,9 +33,10 @@ def _problems():
             vp = inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], rng.uniform(0.5, 2.0))
         else:
             vp = inputs.deformation_params(rng.uniform(1.5, 2.5), 1.0)
-        q0 = inputs.config_local_deformation(N=N, n_random=T).tracers(X)[:, :T]
-        out.append(dict(X=X, q0=q0, n=n, ell=ell, power=p, mode=mode, precision=prec, vk=vk, vp=vp,
-                        dt=1.0 / 50))
+        tr = inputs.config_local_deformation(N=N, n_random=T).tracers
+        q0fn = lambda P, tr=tr, T=T: tr(P)[:, :T]  # noqa: E731
+        out.append(dict(X=X, q0=q0fn(X), q0fn=q0fn, n=n, ell=ell, power=p, mode=mode, precision=prec, vk=vk,
+                        vp=vp, dt=1.0 / 50))
     return out
 
 
@@ -105,3 +109,23 @@ def test_batch_graph_eager_autotune_and_membership_changes():
     np.testing.assert_array_equal(b1.get_q(new[1]), _ctx(probs[5], 3))
     b1.close()
     b2.close()
+
+
+def test_batch_matches_oracle(orc):
+    """Every problem of the batch (n = 31 / 55 / 84, direct and centre stencils, FP64 and
+    mixed, rotation and deformation) against the oracle's run of Algorithm 1."""
+    probs = _problems()
+    S = 6
+    s = torch.cuda.Stream()
+    b = rbfsl.Batch(0, stream=s)
+    ids = [_add(b, P) for P in probs]
+    b.step(S)
+    got = [b.get_q(i) for i in ids]
+    b.close()
+    for k, (P, g) in enumerate(zip(probs, got)):
+        ref = orc.local_run(P["X"], P["q0"], P["n"], P["ell"], P["power"], P["vk"], P["vp"], P["dt"], S,
+                            mode=P["mode"])
+        ex = _parity.exact_field(P["q0fn"], P["X"], P["vk"], P["vp"], S * P["dt"])
+        strict = P["precision"] == rbfsl.FP64 and P["n"] == 31
+        _parity.check_run(f"batch[{k}] N={P['X'].shape[0]} n={P['n']} mode={P['mode']} prec={P['precision']}",
+                          g, ref, ex, strict)

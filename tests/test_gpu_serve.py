@@ -1,5 +1,6 @@
 """Serving loop: requests admitted by a device-memory budget with continuous batching. Each
-request's result must be bit-identical alone and in the mix (local-stencil requests share the
+request's result must match the oracle's run of the same solve (criteria in tests/_parity.py)
+and be bit-identical alone and in the mix (local-stencil requests share the
 batched persistent launch; RBF-PU requests run on their own streams), and admission must keep
 the charged bytes within the budget."""
 import math
@@ -11,6 +12,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from paper_1804_01609_gb300 import inputs, rbfsl  # noqa: E402
+
+import _parity  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -30,10 +33,11 @@ def _requests():
         X = inputs.nodes(N, 300 + k)
         vp = (inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], 1.0) if vk == 0
               else inputs.deformation_params(2.0, 1.0))
-        q0 = inputs.config_local_deformation(N=N, n_random=T).tracers(X)[:, :T]
+        tr = inputs.config_local_deformation(N=N, n_random=T).tracers
+        q0fn = lambda P, tr=tr, T=T: tr(P)[:, :T]  # noqa: E731
         C = inputs.fibonacci_nodes(math.ceil(2.5 * N / n)) if method == rbfsl.PU else None
-        out.append(dict(X=X, q0=q0, n=n, ell=ell, power=p, vel_kind=vk, vel_params=vp, dt=1 / 40,
-                        steps=steps, method=method, mode=mode, precision=prec, centers=C))
+        out.append(dict(X=X, q0=q0fn(X), q0fn=q0fn, n=n, ell=ell, power=p, vel_kind=vk, vel_params=vp,
+                        dt=1 / 40, steps=steps, method=method, mode=mode, precision=prec, centers=C))
     return out
 
 
@@ -98,3 +102,34 @@ def test_budget_admission_and_refusal():
         _submit(tiny, reqs[0])
     assert e.value.code == rbfsl.ENOMEM
     tiny.close()
+
+
+def _oracle_run(orc, r):
+    if r["method"] == rbfsl.LOCAL:
+        return orc.local_run(r["X"], r["q0"], r["n"], r["ell"], r["power"], r["vel_kind"], r["vel_params"],
+                             r["dt"], r["steps"], mode=r["mode"])
+    pu = orc.PUInterpolator(r["X"], r["centers"], r["n"], r["ell"], r["power"])
+    q = r["q0"]
+    for m in range(r["steps"]):
+        q = pu.apply(orc.trace_rk4(r["X"], r["vel_kind"], r["vel_params"], (m + 1) * r["dt"], r["dt"]), q)
+    return q
+
+
+def test_served_results_match_oracle(orc):
+    """Every request of the mix (local direct / centre stencils and RBF-PU, FP64 and mixed)
+    served together, each against the oracle's run of the same solve."""
+    reqs = _requests()
+    srv = rbfsl.Server(0, budget_bytes=40 * 10 ** 9, max_slots=8)
+    tickets = []
+    for r in reqs:
+        tickets.append(_submit(srv, r))
+        time.sleep(0.003)
+    srv.wait_idle(300)
+    got = [srv.result(t)[0] for t in tickets]
+    srv.close()
+    for k, (r, g) in enumerate(zip(reqs, got)):
+        ref = _oracle_run(orc, r)
+        ex = _parity.exact_field(r["q0fn"], r["X"], r["vel_kind"], r["vel_params"], r["steps"] * r["dt"])
+        strict = r["precision"] == rbfsl.FP64 and r["method"] == rbfsl.LOCAL and r["n"] == 31
+        _parity.check_run(f"served[{k}] method={r['method']} N={r['X'].shape[0]} n={r['n']} "
+                          f"prec={r['precision']}", g, ref, ex, strict)
