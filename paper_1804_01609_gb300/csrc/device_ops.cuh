@@ -388,6 +388,67 @@ __device__ __forceinline__ int tri_row(int e) {
     return r;
 }
 
+// |v| / 2^s as an FP32 number, from the bits of the double v with integer operations only
+// (the exponent rebased by s, the fraction truncated to 23 bits; 0 below FP32's normal range,
+// +inf above it, NaN for NaN). Used for the pivot tests, so that the deciding warp's serial chain
+// does not wait on the FP64 pipe, which the other points' trailing updates keep busy.
+__device__ __forceinline__ float mag_f32(long long bits, int s) {
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0x7ff) return __int_as_float((bits & 0xfffffffffffffLL) ? 0x7fc00000 : 0x7f800000);
+    if (e == 0) return 0.0f;
+    const int fe = e - s - 1023 + 127;
+    if (fe <= 0) return 0.0f;
+    if (fe >= 255) return __int_as_float(0x7f800000);
+    return __int_as_float((fe << 23) | (int)((bits >> 29) & 0x7fffff));
+}
+
+// Unbiased exponent of a finite nonzero double (0 for zero and subnormals).
+__device__ __forceinline__ int exp_of(long long bits) {
+    const int e = (int)((bits >> 52) & 0x7ff);
+    return e == 0 ? 0 : e - 1023;
+}
+
+// Warp-wide maximum of non-negative 64-bit keys (the bit patterns of |a|) with the smallest
+// row attaining it: three redux.sync reductions on the 32-bit halves and the row, instead of
+// five rounds of 64-bit shuffles (10% of the DIRECT weights launch at m = 109). Lanes without a candidate pass key 0 and row m (a real zero
+// entry then wins by its smaller row; a column with no rows gives key 0 and row m).
+__device__ __forceinline__ void warp_max_key_row(long long &key, int &row) {
+    const unsigned hi = (unsigned)((unsigned long long)key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    const bool top = hi == mhi && lo == mlo;
+    row = (int)__reduce_min_sync(0xffffffffu, top ? (unsigned)row : 0xffffffffu);
+    key = (long long)(((unsigned long long)mhi << 32) | mlo);
+}
+
+__device__ __forceinline__ long long warp_max_key(long long key) {
+    const unsigned hi = (unsigned)((unsigned long long)key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+    const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+    return (long long)(((unsigned long long)mhi << 32) | mlo);
+}
+
+// 1 / d by Newton-Raphson iteration r <- r + r (1 - d r) (the classical reciprocal iteration,
+// each step doubling the correct bits) from an FP32 seed: the reciprocal of d's leading 24
+// significand bits (rcp.approx.f32, ~23 correct bits) with d's exponent negated, then two
+// FMA-based steps in FP64, ~1 ulp. Zero, subnormal, huge or non-finite d take the division.
+__device__ __forceinline__ double recip_nr(double d) {
+    const long long b = __double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e < 2 || e > 2044) return 1.0 / d;
+    const float mf = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));  // in [1, 2)
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(mf));                     // in (0.5, 1]
+    const int fb = __float_as_int(rf);
+    const long long re = (long long)(((fb >> 23) & 0xff) - 127) + 1023 - (e - 1023);
+    double r = __longlong_as_double((b & (long long)0x8000000000000000ULL) | (re << 52) |
+                                    ((long long)(fb & 0x7fffff) << 29));
+    double t = fma(-d, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-d, r, 1.0);
+    return fma(r, t, r);
+}
+
 // Weights of one point by a group of NW warps (thread t of the group). Assembles the packed
 // lower triangle of A~ and b (Eqs. rbf_poly, rbf_poly_linsys), factorises with Bunch-Kaufman
 // pivoting (alpha = (1 + sqrt 17) / 8; column maximum lambda at row r (smaller row on a tie),
@@ -395,7 +456,13 @@ __device__ __forceinline__ int tri_row(int e) {
 // alpha lambda^2, 1 x 1 pivot r if |a_rr| >= alpha sigma, else the 2 x 2 pivot (k, r)),
 // applying the forward substitution to b as it goes, then solves D and L^T. Warp 0 takes the
 // pivot decisions, interchanges and multipliers; all warps update the trailing triangle, each
-// element by the same FMAs whichever thread takes it, so any NW gives the same bits. Returns
+// element by the same FMAs whichever thread takes it, so any NW gives the same bits. The
+// decision's serial chain keeps off the FP64 pipe where it can (that pipe is the SM's
+// bottleneck and queues the other points' updates): the three pivot tests compare FP32 copies
+// of the magnitudes rescaled by lambda's exponent (alpha is then honoured to ~1e-7, which the
+// method's stability bound does not notice), and pivots are inverted by recip_nr. Each diagonal
+// block is overwritten by its inverse once its multipliers are formed, so the final D solve
+// multiplies instead of dividing. Returns
 // RBFSL_OK with the weights w (n doubles, stencil order) in `out` (valid for warp 0),
 // RBFSL_EKNN for a stencil index < 0, RBFSL_ESINGULAR for two coincident stencil nodes or a
 // zero or non-finite pivot.
@@ -435,9 +502,14 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
         int r, c;
         if (e < n - 1 - f) { r = f + 1 + e; c = f; } else { r = e + 1; c = n - 1 - f; }
         const double dx = cx[r] - cx[c], dy = cy[r] - cy[c], dz = cz[r] - cz[c];
-        const double d2 = dx * dx + dy * dy + dz * dz;
+        const double d2 = fma(dz, dz, fma(dy, dy, dx * dx));
         if (d2 == 0.0) st[0] = 2;  // two coincident nodes: two equal rows, singular
-        P[tri(r) + c] = phs_from_d2(d2, half);
+        double v = sqrt(d2), q = d2;  // r^p = r (r^2)^half, the power by repeated squaring
+        for (int h = half; h > 0; h >>= 1) {
+            if (h & 1) v *= q;
+            if (h > 1) q *= q;
+        }
+        P[tri(r) + c] = v;
     }
     for (int j = t; j < n; j += GT) {
         P[tri(j) + j] = 0.0;
@@ -457,22 +529,20 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
     for (int k = 0; k < m;) {
         if (warp == 0) {
             // ---- pivot decision: lambda = max |a_ik| below the diagonal, r its row
-            long long best = -1;
+            long long best = 0;
             int r = m;
             for (int i = k + 1 + lane; i < m; i += kWarp) {
                 const long long v = __double_as_longlong(P[tri(i) + k]) & 0x7fffffffffffffffLL;
-                if (v > best) { best = v; r = i; }
+                if (v > best || r == m) { best = v; r = i; }
             }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, r, off);
-                if (ob > best || (ob == best && oi < r)) { best = ob; r = oi; }
-            }
-            const double lam = best < 0 ? 0.0 : __longlong_as_double(best);
-            const double akk = fabs(P[tri(k) + k]);
+            warp_max_key_row(best, r);
+            const int sx = best > 0 ? exp_of(best) : 0;  // the tests' scale 2^sx: lambda in [1, 2)
+            const float lam = best > 0 ? mag_f32(best, sx) : 0.0f;
+            const long long kb = __double_as_longlong(P[tri(k) + k]) & 0x7fffffffffffffffLL;
+            const float akk = mag_f32(kb, sx);
+            constexpr float kAlphaF = (float)kAlpha;
             int s = 1, piv = k;
-            if (!(akk >= kAlpha * lam)) {
+            if (!(akk >= kAlphaF * lam)) {
                 // sigma: max off-diagonal |a| in row / column r (integer compare of the bits)
                 long long sb = 0;
                 for (int c = k + lane; c < m; c += kWarp) {
@@ -480,15 +550,11 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
                     const long long v = __double_as_longlong(c < r ? P[tri(r) + c] : P[tri(c) + r]) & 0x7fffffffffffffffLL;
                     sb = v > sb ? v : sb;
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const long long o = __shfl_xor_sync(0xffffffffu, sb, off);
-                    sb = o > sb ? o : sb;
-                }
-                const double sg = __longlong_as_double(sb);
-                if (akk * sg >= kAlpha * lam * lam) {
+                sb = warp_max_key(sb);
+                const float sg = mag_f32(sb, sx);
+                if (akk * sg >= kAlphaF * lam * lam) {
                     s = 1;
-                } else if (fabs(P[tri(r) + r]) >= kAlpha * sg) {
+                } else if (mag_f32(__double_as_longlong(P[tri(r) + r]), sx) >= kAlphaF * sg) {
                     piv = r;
                 } else {
                     s = 2;
@@ -516,12 +582,14 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
                 __syncwarp();
             }
             // ---- multipliers of the trailing rows
+            auto bad_bits = [](double v) {  // zero or non-finite
+                const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+                return b == 0 || b >= 0x7ff0000000000000LL;
+            };
             if (s == 1) {
                 const double d = P[tri(k) + k];
-                const bool bad = !(d != 0.0) || !isfinite(d);
-                double dinv = 0.0;
-                if (lane == 0) dinv = 1.0 / d;  // one division, broadcast
-                dinv = __shfl_sync(0xffffffffu, dinv, 0);
+                const bool bad = bad_bits(d);
+                const double dinv = recip_nr(d);  // every lane, same bits
                 for (int i = k + 1 + lane; i < m; i += kWarp) {
                     const double c = P[tri(i) + k];
                     u0[i] = c;
@@ -529,35 +597,42 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
                     l0[i] = l;
                     P[tri(i) + k] = l;
                 }
-                if (lane == 0) { ptype[k] = 1; st[1] = 1; if (bad) st[0] = 2; }
+                __syncwarp();
+                if (lane == 0) { P[tri(k) + k] = dinv; ptype[k] = 1; st[1] = 1; if (bad) st[0] = 2; }
             } else {
                 const double a11 = P[tri(k) + k], a21 = P[tri(k + 1) + k], a22 = P[tri(k + 1) + k + 1];
-                const double det = a11 * a22 - a21 * a21;
-                const bool bad = !(det != 0.0) || !isfinite(det);
-                double idet = 0.0;
-                if (lane == 0) idet = 1.0 / det;
-                idet = __shfl_sync(0xffffffffu, idet, 0);
+                const double det = fma(a11, a22, -(a21 * a21));
+                const bool bad = bad_bits(det);
+                const double idet = recip_nr(det);
+                // D^-1 = [[e22, -e21], [-e21, e11]]
+                const double e11 = a11 * idet, e21 = a21 * idet, e22 = a22 * idet;
                 for (int i = k + 2 + lane; i < m; i += kWarp) {
                     const double c0 = P[tri(i) + k], c1 = P[tri(i) + k + 1];
                     u0[i] = c0;
                     u1[i] = c1;
-                    const double L0 = (c0 * a22 - c1 * a21) * idet, L1 = (c1 * a11 - c0 * a21) * idet;
+                    const double L0 = fma(c0, e22, -(c1 * e21)), L1 = fma(c1, e11, -(c0 * e21));
                     l0[i] = L0;
                     l1[i] = L1;
                     P[tri(i) + k] = L0;
                     P[tri(i) + k + 1] = L1;
                 }
-                if (lane == 0) { ptype[k] = 2; ptype[k + 1] = 0; st[1] = 2; if (bad) st[0] = 2; }
+                __syncwarp();
+                if (lane == 0) {
+                    P[tri(k) + k] = e22;
+                    P[tri(k + 1) + k] = -e21;
+                    P[tri(k + 1) + k + 1] = e11;
+                    ptype[k] = 2; ptype[k + 1] = 0; st[1] = 2; if (bad) st[0] = 2;
+                }
             }
-            if (lane == 0 && lam == 0.0 && akk == 0.0) st[0] = 2;  // a zero column: singular
+            if (lane == 0 && best <= 0 && kb == 0) st[0] = 2;  // a zero column: singular
         }
         gsync();
         if (st[0]) return RBFSL_ESINGULAR;
         // ---- trailing update, rows and columns base..m-1 (lower triangle), and the rhs. Each
-        // thread takes four elements of the flattened triangle at a time (all loads, then the
-        // FMAs, then the stores) so that several DFMAs per warp are in flight.
+        // thread takes two elements of the flattened triangle at a time (all loads, then the
+        // FMAs, then the stores; measured at m = 109 against one, four and eight).
         const int s = st[1], base = k + s, Rr = m - base, E = Rr * (Rr + 1) / 2;
-        constexpr int U = 4;
+        constexpr int U = 2;
         for (int e0 = t; e0 < E; e0 += U * GT) {
             int addr[U], ii[U], jj[U];
             double v[U], a0[U], b0[U], a1[U], b1[U];
@@ -600,15 +675,14 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
     }
     if (warp != 0) return RBFSL_OK;
     // ---- D z = y (blocks independent), then L^T x = z column by column
-    for (int p = lane; p < m; p += kWarp) {
+    for (int p = lane; p < m; p += kWarp) {  // the diagonal blocks hold their inverses
         if (ptype[p] == 1) {
-            y[p] = y[p] / P[tri(p) + p];
+            y[p] = y[p] * P[tri(p) + p];
         } else if (ptype[p] == 2) {
-            const double a11 = P[tri(p) + p], a21 = P[tri(p + 1) + p], a22 = P[tri(p + 1) + p + 1];
-            const double det = a11 * a22 - a21 * a21;
+            const double f11 = P[tri(p) + p], f21 = P[tri(p + 1) + p], f22 = P[tri(p + 1) + p + 1];
             const double y0 = y[p], y1 = y[p + 1];
-            y[p] = (a22 * y0 - a21 * y1) / det;
-            y[p + 1] = (a11 * y1 - a21 * y0) / det;
+            y[p] = fma(f11, y0, f21 * y1);
+            y[p + 1] = fma(f22, y1, f21 * y0);
         }
     }
     __syncwarp();
