@@ -43,8 +43,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson arrivals) measurement")
+    ap.add_argument("--served-requests", type=int, default=128, help="requests of the served leg")
+    ap.add_argument("--served-steps", type=int, nargs=2, default=[50, 120], metavar=("MIN", "MAX"),
+                    help="steps per served request, drawn uniformly from [MIN, MAX]")
     ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq", "tceval",
-                                                  "cardinal"],
+                                                  "cardinal", "served"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
     ap.add_argument("--repeat", type=int, default=3)
@@ -150,8 +153,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
-# capture of this kernel version (profiles/weights_direct_N40962_n84.md).
-WEIGHTS_DRAM_BYTES = 15.81e6
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel version this file ships
+# with; None when no capture of that version exists.
+WEIGHTS_DRAM_BYTES = 16.26e6 + 512
 
 
 def weights_flops(m):
@@ -227,26 +231,37 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def cpu_baseline(w, budget_s=10.0):
+def cpu_baseline(w, budget_s=10.0, single_budget_s=5.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded sample: departure
     points of one step for all nodes, then brute-force k-NN + GEPP weights + gather for the
-    first S nodes, with S sized to ~budget_s of work."""
+    first S nodes, with S sized to ~budget_s of work; timed on all cores and on one core."""
     import oracle
     oracle.build()
     X = w.X
     q = w.q0()
     Xi = oracle.trace_rk4(X, w.vel_kind, w.vel_params, w.dt, w.dt)
-    S = 256
-    t0 = time.perf_counter()
-    oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
-    dt0 = time.perf_counter() - t0
-    S = int(min(w.N, max(256, S * budget_s / max(dt0, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
-    el = time.perf_counter() - t0
-    return {"value": S / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+
+    def timed(budget):
+        S = 64
+        t0 = time.perf_counter()
+        oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
+        dt0 = time.perf_counter() - t0
+        S = int(min(w.N, max(64, S * budget / max(dt0, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.local_apply(X, Xi[:S], q, w.n, w.ell, oracle.PHS, float(w.power))
+        return S, time.perf_counter() - t0
+
+    oracle.set_threads(0)
+    S, el = timed(budget_s)
+    cores = oracle.num_threads()
+    oracle.set_threads(1)
+    S1, el1 = timed(single_budget_s)
+    oracle.set_threads(0)
+    return {"value": S / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{S} of {w.N} node-updates of one SL step (brute-force k-NN, GEPP, "
-                      f"gather of {w.T} tracers; FP64 C + OpenMP); {el:.1f} s"}
+                      f"gather of {w.T} tracers; FP64 C + OpenMP); {el:.1f} s",
+            "single_thread": {"value": S1 / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"{S1} node-updates of the same step, one thread; {el1:.1f} s"}}
 
 
 # ----------------------------------------------------------------------------- W.q roofline
@@ -570,95 +585,196 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
 
 
 # ----------------------------------------------------------------------------- batched
-def bench_batched(rbfsl, torch, stream, precision, steps=2):
+def bench_batched(rbfsl, torch, stream, steps=10, seq_steps=3):
     """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
     {(31,2), (55,3), (84,4)} with r^(2 ell + 1), 1-16 tracers, own rotation or deformation),
-    direct stencils, one persistent fused kernel per step under a CUDA graph."""
+    direct stencils, one persistent fused kernel per step under a CUDA graph, mixed precision
+    and FP64; against the same problems stepped one after another through single-problem
+    contexts (mixed); per-problem relative l2 of the mixed result against the FP64 one."""
     from paper_1804_01609_gb300 import inputs
     specs = inputs.batched_problems(64)
-    b = rbfsl.Batch(0, stream=stream)
-    nodes = 0
+    probs = []
     for sp in specs:
         X = inputs.nodes(sp["N"], sp["seed"])
         rng = np.random.default_rng(sp["seed"])
         fns = [inputs.plane_wave_field(rng, 8.0) for _ in range(sp["T"])]
-        q0 = np.stack([f(X) for f in fns], axis=1)
-        b.add(X, q0, sp["n"], sp["ell"], sp["power"], sp["vel_kind"], sp["vel_params"], 1.0 / 100,
-              mode=rbfsl.DIRECT, precision=precision)
-        nodes += sp["N"]
-    choices = b.autotune()
-    b.step(1)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    b.close()
-    return {"problems": len(specs), "nodes": nodes, "value": nodes / (ms / 1e3), "ms_per_step": ms,
-            "tile_shapes": [list(c) for c in choices]}
+        probs.append((sp, X, np.stack([f(X) for f in fns], axis=1)))
+    nodes = sum(sp["N"] for sp, _, _ in probs)
+    out = {"problems": len(probs), "nodes": nodes, "steps": steps}
+    finals = {}
+    for prec, name in ((rbfsl.MIXED, "mixed"), (rbfsl.FP64, "fp64")):
+        b = rbfsl.Batch(0, stream=stream)
+        ids = [b.add(X, q0, sp["n"], sp["ell"], sp["power"], sp["vel_kind"], sp["vel_params"], 1.0 / 100,
+                     mode=rbfsl.DIRECT, precision=prec) for sp, X, q0 in probs]
+        choices = b.autotune()
+        b.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        finals[name] = [b.get_q(i) for i in ids]
+        b.close()
+        out[name] = {"value": nodes / (ms / 1e3), "ms_per_step": ms, "tile_shapes": [list(c) for c in choices]}
+    # the same problems one after another through contexts (mixed), seq_steps steps each
+    seq_ms = 0.0
+    for sp, X, q0 in probs:
+        ctx = rbfsl.Context(0, stream=stream)
+        ctx.set_nodes(X)
+        ctx.set_velocity(sp["vel_kind"], sp["vel_params"])
+        ctx.set_method(rbfsl.LOCAL, rbfsl.DIRECT)
+        ctx.set_stencil_size(sp["n"])
+        ctx.set_sh_degree(sp["ell"])
+        ctx.set_kernel(rbfsl.PHS, sp["power"])
+        ctx.set_precision(rbfsl.MIXED)
+        ctx.set_dt(1.0 / 100)
+        ctx.set_tracers(q0)
+        ctx.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(seq_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1) / seq_steps
+        ctx.close()
+    d = [rel_l2(a, b) for a, b in zip(finals["mixed"], finals["fp64"])]
+    out["sequential_contexts_mixed"] = {"ms_per_step": seq_ms, "value": nodes / (seq_ms / 1e3),
+                                        "steps_timed_per_problem": seq_steps}
+    out["batched_over_sequential"] = seq_ms / out["mixed"]["ms_per_step"]
+    out["accuracy_mixed_vs_fp64"] = {"steps": steps + 1, "rel_l2_max": float(max(d)),
+                                     "rel_l2_median": float(np.median(d))}
+    return out
 
 
 # ----------------------------------------------------------------------------- served
-def bench_served(rbfsl, precision, R=32, rate=200.0, seed=1804 * 100 + 5):
-    """Poisson arrivals (mean `rate`/s) of R transport solves, half local (centre stencils,
-    (n, ell) from {(31,2),(55,3),(84,4)}) and half RBF-PU (~100 nodes per patch, ell = 3), N from
-    {642, 2562, 10242, 40962}, 1-16 tracers, 50-200 steps; device-memory budget 150 GB."""
-    import threading
+def served_requests(R, rate, Ns, steps, seed, rbfsl):
+    """R transport solves with Poisson arrival times (mean `rate`/s): half local (centre
+    stencils, (n, ell) from {(31,2),(55,3),(84,4)}, r^(2 ell + 1)) and half RBF-PU (~100 nodes per
+    patch, ell = 3, r^7, Wendland weights, a = 2.5), N drawn from Ns, 1-16 smooth tracers, steps
+    drawn from [steps[0], steps[1]], each its own tilted rotation over one period. Returns
+    (arrival time, request, exact-solution function)."""
     from paper_1804_01609_gb300 import inputs
     rng = np.random.default_rng(seed)
     reqs = []
     t = 0.0
     for k in range(R):
         t += rng.exponential(1.0 / rate)
-        N = int(rng.choice([642, 2562, 10242, 40962]))
+        N = int(rng.choice(Ns))
         T = int(rng.integers(1, 17))
-        steps = int(rng.integers(50, 201))
+        S = int(rng.integers(steps[0], steps[1] + 1))
         X = inputs.nodes(N, seed * 100 + k)
         fns = [inputs.plane_wave_field(rng, 8.0) for _ in range(T)]
         q0 = np.stack([f(X) for f in fns], axis=1)
-        vp = inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], float(rng.uniform(0.5, 2.0)))
+        vp = inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], 1.0)
         if k % 2 == 0:
             n, ell = [(31, 2), (55, 3), (84, 4)][int(rng.integers(0, 3))]
-            reqs.append((t, dict(X=X, q0=q0, n=n, ell=ell, power=2 * ell + 1, vel_kind=0, vel_params=vp,
-                                 dt=1.0 / steps, steps=steps, method=rbfsl.LOCAL, mode=rbfsl.CENTER,
-                                 precision=precision, centers=None)))
+            r = dict(X=X, q0=q0, n=n, ell=ell, power=2 * ell + 1, vel_kind=0, vel_params=vp, dt=1.0 / S,
+                     steps=S, method=rbfsl.LOCAL, mode=rbfsl.CENTER, centers=None)
         else:
             n = 100
-            C = inputs.fibonacci_nodes(int(np.ceil(2.5 * N / n)))
-            reqs.append((t, dict(X=X, q0=q0, n=n, ell=3, power=7, vel_kind=0, vel_params=vp,
-                                 dt=1.0 / steps, steps=steps, method=rbfsl.PU, mode=rbfsl.DIRECT,
-                                 precision=precision, centers=C)))
-    srv = rbfsl.Server(0, budget_bytes=150 * 10 ** 9, max_slots=64)
+            r = dict(X=X, q0=q0, n=n, ell=3, power=7, vel_kind=0, vel_params=vp, dt=1.0 / S, steps=S,
+                     method=rbfsl.PU, mode=rbfsl.DIRECT, centers=inputs.fibonacci_nodes(int(np.ceil(2.5 * N / n))))
+        reqs.append((t, r, fns))
+    return reqs
+
+
+def serve_once(rbfsl, reqs, precision, budget=150 * 10 ** 9, slots=64):
+    import threading
+    srv = rbfsl.Server(0, budget_bytes=budget, max_slots=slots)
     tickets = []
 
     def submitter():
         t0 = time.perf_counter()
-        for ta, r in reqs:
+        for ta, r, _ in reqs:
             d = ta - (time.perf_counter() - t0)
             if d > 0:
                 time.sleep(d)
             tickets.append(srv.submit(r["X"], r["q0"], r["n"], r["ell"], r["power"], r["vel_kind"],
                                       r["vel_params"], r["dt"], r["steps"], method=r["method"],
-                                      mode=r["mode"], precision=r["precision"], centers=r["centers"]))
+                                      mode=r["mode"], precision=precision, centers=r["centers"]))
 
     th = threading.Thread(target=submitter)
     th.start()
     th.join()
-    srv.wait_idle(1200)
-    stats = [srv.result(tk, raise_on_failure=False)[1] for tk in tickets]
-    errors = sorted({s.message.decode() for s in stats if s.status != 0})
+    srv.wait_idle(3600)
+    res = [srv.result(tk, raise_on_failure=False) for tk in tickets]
     info = srv.info()
     srv.close()
-    lat = np.array([s.finish_s - s.submit_s for s in stats])
-    span = max(s.finish_s for s in stats) - min(s.submit_s for s in stats)
-    nu = sum(s.node_updates for s in stats)
-    return {"requests": R, "arrival_rate_per_s": rate, "node_updates": int(nu),
-            "value": nu / span, "wall_s": span, "latency_p50_s": float(np.percentile(lat, 50)),
-            "latency_p99_s": float(np.percentile(lat, 99)), "failed": int(sum(s.status != 0 for s in stats)),
-            "errors": errors[:3],
-            "peak_bytes": int(info.peak_bytes), "ticks": int(info.ticks)}
+    return res, info
+
+
+def bench_served(rbfsl, R=128, rate=200.0, Ns=(642, 2562, 10242, 40962, 163842, 655362), steps=(50, 120),
+                 seed=1804 * 100 + 5):
+    """The served workload (requests as in served_requests, device-memory budget 150 GB, 64
+    slots), once in mixed precision and once in FP64 on the same requests. Reports per precision
+    the achieved node-updates/s, p50/p99 latency (submission to result), the offered load (node
+    updates of all requests over their arrival span) and the admission peak; per request the
+    relative l2 of the mixed result against the FP64 one and both errors against the exact
+    solution (one full rotation: the initial field); the FP64 results of the smallest requests
+    against the oracle's run of the same solve."""
+    reqs = served_requests(R, rate, Ns, steps, seed, rbfsl)
+    arrivals = [t for t, _, _ in reqs]
+    work = sum(r["X"].shape[0] * r["steps"] for _, r, _ in reqs)
+    offered = work / max(arrivals[-1] - arrivals[0], 1e-9)
+    out = {"requests": R, "arrival_rate_per_s": rate, "N": list(Ns), "steps": list(steps),
+           "node_updates": int(work), "offered_node_updates_per_s": offered}
+    results, stats_of = {}, {}
+    for prec, name in ((rbfsl.MIXED, "mixed"), (rbfsl.FP64, "fp64")):
+        res, info = serve_once(rbfsl, reqs, prec)
+        stats = [st for _, st in res]
+        results[name] = [q for q, _ in res]
+        stats_of[name] = stats
+        lat = np.array([st.finish_s - st.submit_s for st in stats])
+        span = max(st.finish_s for st in stats) - min(st.submit_s for st in stats)
+        nu = sum(st.node_updates for st in stats)
+        out[name] = {"value": nu / span, "wall_s": span, "latency_p50_s": float(np.percentile(lat, 50)),
+                     "latency_p99_s": float(np.percentile(lat, 99)),
+                     "failed": int(sum(st.status != 0 for st in stats)),
+                     "requests_with_failed_points": int(sum(st.failed_points > 0 for st in stats)),
+                     "errors": sorted({st.message.decode() for st in stats if st.status != 0})[:3],
+                     "peak_bytes": int(info.peak_bytes), "budget_bytes": int(info.budget_bytes),
+                     "ticks": int(info.ticks)}
+    ratios, d, bad = [], [], []
+    for k, ((_, r, fns), qm, q64) in enumerate(zip(reqs, results["mixed"], results["fp64"])):
+        desc = {"request": k, "method": "local" if r["method"] == rbfsl.LOCAL else "pu", "N": r["X"].shape[0],
+                "n": r["n"], "ell": r["ell"], "steps": r["steps"], "T": r["q0"].shape[1],
+                "failed_points": {nm: int(stats_of[nm][k].failed_points) for nm in ("mixed", "fp64")}}
+        fin = {nm: q is not None and bool(np.isfinite(q).all()) for nm, q in (("mixed", qm), ("fp64", q64))}
+        if not (fin["mixed"] and fin["fp64"]):
+            bad.append(dict(desc, finite=fin, max_abs={nm: (float(np.nanmax(np.abs(q))) if q is not None else None)
+                                                       for nm, q in (("mixed", qm), ("fp64", q64))}))
+            continue
+        e64 = rel_l2(q64, r["q0"])
+        if not e64 < 0.5:  # the FP64 run itself diverged (stencil systems beyond FP64, see DESIGN)
+            bad.append(dict(desc, fp64_l2_vs_exact=e64, mixed_l2_vs_exact=rel_l2(qm, r["q0"])))
+            continue
+        d.append(rel_l2(qm, q64))
+        ratios.append(abs(rel_l2(qm, r["q0"]) - e64) / e64)
+    out["accuracy"] = {"compared": len(d), "mixed_vs_fp64_rel_l2_max": float(max(d)) if d else None,
+                       "mixed_vs_fp64_rel_l2_median": float(np.median(d)) if d else None,
+                       "mixed_error_excess_over_fp64_max": float(max(ratios)) if ratios else None,
+                       "all_within_1pct_of_fp64_error": bool(ratios and max(ratios) <= 0.01),
+                       "diverged_or_nonfinite": bad[:12], "diverged_or_nonfinite_count": len(bad)}
+    import oracle
+    oracle.build()
+    small = [(r, q64) for (_, r, _), q64 in zip(reqs, results["fp64"]) if r["X"].shape[0] == min(Ns)][:4]
+    checks = []
+    for r, q64 in small:
+        if r["method"] == rbfsl.LOCAL:
+            ref = oracle.local_run(r["X"], r["q0"], r["n"], r["ell"], r["power"], r["vel_kind"], r["vel_params"],
+                                   r["dt"], r["steps"], mode=oracle.CENTER)
+        else:
+            pu = oracle.PUInterpolator(r["X"], r["centers"], r["n"], r["ell"], r["power"])
+            ref = r["q0"]
+            for m in range(r["steps"]):
+                ref = pu.apply(oracle.trace_rk4(r["X"], r["vel_kind"], r["vel_params"], (m + 1) * r["dt"], r["dt"]), ref)
+        checks.append({"method": "local" if r["method"] == rbfsl.LOCAL else "pu", "N": r["X"].shape[0],
+                       "steps": r["steps"], "fp64_vs_oracle_rel_l2": rel_l2(q64, ref)})
+    out["oracle_check_smallest"] = checks
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -706,6 +822,10 @@ def run_case(args):
         flush = torch.empty(64 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         r = bench_wq_hbm(rbfsl, torch, stream, flush, K=args.repeat)
         print(f"case wq: {json.dumps(r)}", flush=True)
+        return
+    if args.case == "served":  # the served leg alone (--served-requests, --served-steps)
+        r = bench_served(rbfsl, R=args.served_requests, steps=tuple(args.served_steps))
+        print(f"case served: {json.dumps(json_safe(r))}", flush=True)
         return
     if args.case == "tceval":  # the tensor-core global evaluation at the global workload's size
         from paper_1804_01609_gb300 import inputs
@@ -912,6 +1032,22 @@ def main():
             center["fp64"]["l2_vs_exact"] = rel_l2(qc64, q0)
             center["mixed"]["l2_vs_exact"] = rel_l2(qcmx, q0)
 
+    # the metric's comparison: mixed against FP64 at equal l2 error (the 600-step reversal
+    # returns the field, so the error is against the initial field), for the graded direct
+    # stencils and for the paper's centre stencils
+    equal_acc = {"direct": {"mixed_value": value, "fp64_value": value64,
+                            "mixed_l2_vs_exact": acc.get("mixed_l2_vs_exact"),
+                            "fp64_l2_vs_exact": acc.get("fp64_l2_vs_exact")},
+                 "center": {"mixed_value": center["mixed"]["value"], "fp64_value": center["fp64"]["value"],
+                            "mixed_l2_vs_exact": center["mixed"].get("l2_vs_exact"),
+                            "fp64_l2_vs_exact": center["fp64"].get("l2_vs_exact")}}
+    for v in equal_acc.values():
+        v["mixed_over_fp64_speed"] = v["mixed_value"] / v["fp64_value"]
+        if v["mixed_l2_vs_exact"] is not None:
+            v["mixed_within_1pct_of_fp64_error"] = bool(
+                abs(v["mixed_l2_vs_exact"] - v["fp64_l2_vs_exact"]) <= 0.01 * v["fp64_l2_vs_exact"])
+    equal_acc["center_over_direct_mixed_speed"] = center["mixed"]["value"] / value
+
     wq = bench_wq_hbm(rbfsl, torch, stream, flush)
     glob = bench_global(rbfsl, torch, stream, flush,
                         accuracy_eps=(6.0, 9.0, 24.0) if args.accuracy_steps > 0 else ())
@@ -921,11 +1057,10 @@ def main():
     paper_cases = bench_paper_cases(rbfsl, torch, stream) if args.accuracy_steps > 0 else {}
     batched = {}
     if not args.no_batched:
-        batched = {"mixed": bench_batched(rbfsl, torch, stream, rbfsl.MIXED),
-                   "fp64": bench_batched(rbfsl, torch, stream, rbfsl.FP64)}
+        batched = bench_batched(rbfsl, torch, stream)
     served = {}
     if not args.no_served:
-        served = {"mixed": bench_served(rbfsl, rbfsl.MIXED), "fp64": bench_served(rbfsl, rbfsl.FP64)}
+        served = bench_served(rbfsl, R=args.served_requests, steps=tuple(args.served_steps))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -948,6 +1083,7 @@ def main():
         "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                             "p99": float(np.percentile(step_ms, 99))},
         "fp64": {"value": value64, "ms_per_step": float(step64_ms.mean())},
+        "mixed_vs_fp64_at_equal_l2": equal_acc,
         "center_stencils": center,
         "integrator_at_dt_1_150": integ,
         "global_N10242_T64": glob,
@@ -961,7 +1097,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 Bunch-Kaufman LDL^T, m = 109)",
                      "achieved": w_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": w_tflops / FP64_PEAK_TFLOPS, "traffic": WEIGHTS_DRAM_BYTES,
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write, full launch)",
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write of this kernel version, "
+                                     "full launch; null: not captured for this version)",
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
                      "flops_per_unit": "(2/3) m^3 + 2 m^2 per point (one saddle-point solve, elimination's count)",
                      "kernel_flops_per_unit": "(1/3) m^3 + 2 m^2 (the L D L^T the kernel performs)",

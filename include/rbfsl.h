@@ -442,6 +442,8 @@ typedef struct rbfsl_request_stats {
     size_t device_bytes;                /* the admission estimate charged to the budget */
     int status;                         /* RBFSL_OK or the failure code */
     char message[160];                  /* the failure's message ("" on success) */
+    int64_t failed_points;              /* point-steps with a singular stencil, a failed neighbour
+                                           search or no covering patch (NaN rows in the result) */
 } rbfsl_request_stats;
 typedef struct rbfsl_server_info_t {
     int64_t ticks, queued;

@@ -71,6 +71,7 @@ def lib():
             L = ctypes.CDLL(build())
             sig = {
                 "orc_num_threads": (_I, []),
+                "orc_set_threads": (None, [_I]),
                 "orc_velocity": (None, [_I, _P, _P, _D, _P]),
                 "orc_trace_rk4": (None, [_I, _P, _P, _I64, _D, _D, _P]),
                 "orc_trace_rk5": (None, [_I, _P, _P, _I64, _D, _D, _P]),
@@ -119,6 +120,11 @@ WENDLAND, BSPLINE = 0, 1
 
 
 # ----------------------------------------------------------------------------- tracing
+def set_threads(n):
+    """OpenMP threads of the oracle's parallel loops (n <= 0: all processors)."""
+    lib().orc_set_threads(int(n))
+
+
 def velocity(kind, prm, x, t):
     x = _f64(x); prm = _f64(prm); u = np.empty(3)
     lib().orc_velocity(kind, _ptr(prm), _ptr(x), t, _ptr(u))

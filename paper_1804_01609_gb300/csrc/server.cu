@@ -46,6 +46,7 @@ struct Req {
     cudaStream_t stream = nullptr;
     int done_steps = 0;
     double t_submit = 0, t_admit = 0, t_finish = 0;
+    int64_t failed_points = 0;
     std::vector<double> result;
     std::string err;
 };
@@ -209,8 +210,15 @@ void worker_loop(rbfsl_server *s) {
             if (r->state == 1) {
                 r->result.resize((size_t)r->prob.N * r->prob.T);
                 int rc;
-                if (r->method == RBFSL_LOCAL) rc = rbfsl_batch_get_q(s->batch, r->batch_id, r->result.data());
-                else rc = rbfsl_get_q(r->ctx, r->result.data(), RBFSL_F64, RBFSL_HOST);
+                rbfsl_stats ps{};
+                if (r->method == RBFSL_LOCAL) {
+                    rc = rbfsl_batch_get_q(s->batch, r->batch_id, r->result.data());
+                    if (!rc) rc = rbfsl_batch_problem_stats(s->batch, r->batch_id, &ps);
+                } else {
+                    rc = rbfsl_get_q(r->ctx, r->result.data(), RBFSL_F64, RBFSL_HOST);
+                    if (!rc) rc = rbfsl_get_stats(r->ctx, &ps);
+                }
+                r->failed_points = ps.singular_points + ps.knn_failures + ps.uncovered_points;
                 if (rc) {
                     r->state = rc;
                     r->err = std::string("result: ") + (r->ctx ? rbfsl_last_error(r->ctx) : get_error());
@@ -343,6 +351,7 @@ int rbfsl_server_result(rbfsl_server *s, uint64_t ticket, double *q_out, rbfsl_r
         st->device_bytes = r->bytes;
         st->status = r->state == 2 ? RBFSL_OK : r->state;
         std::snprintf(st->message, sizeof(st->message), "%s", r->err.c_str());
+        st->failed_points = r->failed_points;
     }
     if (r->state != 2) {
         set_error("server_result: the request failed");

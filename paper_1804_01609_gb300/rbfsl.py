@@ -393,7 +393,8 @@ class RequestStats(ctypes.Structure):
     _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
                 ("finish_s", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("node_updates", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("status", ctypes.c_int), ("message", ctypes.c_char * 160)]
+                ("status", ctypes.c_int), ("message", ctypes.c_char * 160),
+                ("failed_points", ctypes.c_int64)]
 
 
 class ServerInfo(ctypes.Structure):

@@ -58,7 +58,7 @@ def test_results_identical_alone_and_in_the_mix():
     mixed = []
     for t in tickets:
         q, st = srv.result(t)
-        assert st.status == 0 and st.finish_s >= st.admit_s >= st.submit_s
+        assert st.status == 0 and st.finish_s >= st.admit_s >= st.submit_s and st.failed_points == 0
         mixed.append(q)
     assert srv.info().ticks >= max(r["steps"] for r in reqs)
     srv.close()
