@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--served-steps", type=int, nargs=2, default=[50, 120], metavar=("MIN", "MAX"),
                     help="steps per served request, drawn uniformly from [MIN, MAX]")
     ap.add_argument("--case", default=None, choices=["weights", "gather", "knn", "trace", "center", "wq", "tceval",
-                                                  "cardinal", "served"],
+                                                  "cardinal", "served", "batched"],
                     help="run one kernel of the workload on --nq points (for profilers); no JSON")
     ap.add_argument("--nq", type=int, default=3040)
     ap.add_argument("--repeat", type=int, default=3)
@@ -493,7 +493,7 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
     steps (set-up excluded, as the paper's cost comparison)."""
     from paper_1804_01609_gb300 import diagnostics, inputs
 
-    def run(w, method, mode=None, precision=rbfsl.FP64, eps=None):
+    def run(w, method, mode=None, precision=rbfsl.FP64, eps=None, a=2.5):
         ctx = rbfsl.Context(0, stream=stream)
         ctx.set_nodes(w.X)
         ctx.set_velocity(w.vel_kind, w.vel_params)
@@ -509,7 +509,7 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
             ctx.set_sh_degree(w.ell)
             ctx.set_kernel(rbfsl.PHS, w.power)
             if method == "pu":
-                ctx.set_pu(inputs.fibonacci_nodes(int(np.ceil(2.5 * w.N / w.n))))
+                ctx.set_pu(inputs.fibonacci_nodes(int(np.ceil(a * w.N / w.n))))
         ctx.set_dt(w.dt)
         ctx.set_tracers(w.q0())
         ctx.step(1)
@@ -554,6 +554,16 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
         nsw[case] = {meth: [dict(run(mk(n, meth), meth, rbfsl.CENTER if meth == "local" else None), n=n)
                             for n in (17, 31, 49, 84)] for meth in ("local", "pu")}
     out["n_sweep_N40962"] = nsw
+
+    # RBF-PU against the nodes per patch n and the overlap a (Eqs. rad_patches, num_patches:
+    # R = 2 sqrt(n / N) fixed by n, M = ceil(a N / n) patches): error and step time, rotation
+    # of the cosine bell at N = 40,962
+    ovl = []
+    for n in (31, 49, 84):
+        for a in (1.5, 2.5, 3.5, 5.0):
+            w = inputs.config_sbr(40962, method="pu", n=n, **({"ell": 3, "power": 7} if n >= 49 else {}))
+            ovl.append(dict(run(w, "pu", a=a), n=n, a=a, patches=int(np.ceil(a * w.N / n))))
+    out["pu_n_a_sweep_N40962"] = ovl
 
     # ten revolutions of the cosine bell with dt = pi/20 (the paper's mass-conservation run):
     # mass error and l2 error after each revolution, N = 40,962, n = 49
@@ -822,6 +832,10 @@ def run_case(args):
         flush = torch.empty(64 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
         r = bench_wq_hbm(rbfsl, torch, stream, flush, K=args.repeat)
         print(f"case wq: {json.dumps(r)}", flush=True)
+        return
+    if args.case == "batched":  # the batched leg alone
+        r = bench_batched(rbfsl, torch, torch.cuda.Stream())
+        print(f"case batched: {json.dumps(json_safe(r))}", flush=True)
         return
     if args.case == "served":  # the served leg alone (--served-requests, --served-steps)
         r = bench_served(rbfsl, R=args.served_requests, steps=tuple(args.served_steps))

@@ -25,6 +25,8 @@ torch = pytest.importorskip("torch")
 
 from paper_1804_01609_gb300 import inputs, rbfsl  # noqa: E402
 
+import _parity  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
@@ -138,6 +140,8 @@ def assert_within_noise_floor(orc, X, I, P, q, got, ell, p, factor=5.0, nrows=30
     alt = np.stack([orc.stencil_weights(Xp, I[r], ell, orc.PHS, float(p), P[r]) @ q[I[r]] for r in rows])
     floor = np.abs(alt - ref).max()
     diff = np.abs(got[rows] - ref).max()
+    _parity.record(test=f"noise floor N={X.shape[0]} n={I.shape[1]} ell={ell} r^{p}", rows=len(rows),
+                   oracle_floor=float(floor), gpu_diff=float(diff), scale=float(np.abs(q).max()))
     assert diff <= factor * floor + 1e-12 * np.abs(q).max(), (diff, floor)
 
 

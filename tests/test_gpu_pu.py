@@ -17,6 +17,8 @@ torch = pytest.importorskip("torch")
 
 from paper_1804_01609_gb300 import inputs, rbfsl  # noqa: E402
 
+import _parity  # noqa: E402
+
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 
@@ -58,6 +60,8 @@ def test_pu_parity_small(orc, wkind):
     s = np.random.default_rng(0).choice([-1.0, 1.0], size=X.shape)
     alt = orc.PUInterpolator(np.nextafter(X, X + s), Om, n, 3, 7, weight_kind=wkind, R=R).apply(P, q)
     floor = np.abs(alt - ref).max()
+    _parity.record(test=f"PU noise floor N={N} n={n} weight={wkind}", oracle_floor=float(floor),
+                   gpu_diff=float(np.abs(got - ref).max()), scale=float(np.abs(q).max()))
     assert np.abs(got - ref).max() <= 5 * floor + 1e-12 * np.abs(q).max()
 
 
@@ -156,6 +160,8 @@ def test_pu_pair_eval(orc, wkind):
     s = np.random.default_rng(0).choice([-1.0, 1.0], size=X.shape)
     alt = orc.PUInterpolator(np.nextafter(X, X + s), Om, n, 3, 7, weight_kind=wkind, R=R).apply(P, q)
     floor = np.abs(alt - ref).max()
+    _parity.record(test=f"PU pairs noise floor N={N} n={n} weight={wkind}", oracle_floor=float(floor),
+                   gpu_diff=float(np.abs(gp - ref).max()), scale=float(scale))
     assert np.abs(gp - ref).max() <= 5 * floor + 1e-10 * scale
     keep = Om[:, 2] > 0.2
     out, st = _gpu_apply(X, Om[keep], R, q, np.array([[0.0, 0.0, -1.0]]), wkind=wkind, pairs=True)
