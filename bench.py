@@ -595,14 +595,15 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
 
 
 # ----------------------------------------------------------------------------- batched
-def bench_batched(rbfsl, torch, stream, steps=10, seq_steps=3):
-    """64 independent local problems (N from {2562, 10242, 40962, 163842}, (n, ell) from
-    {(31,2), (55,3), (84,4)} with r^(2 ell + 1), 1-16 tracers, own rotation or deformation),
-    direct stencils, one persistent fused kernel per step under a CUDA graph, mixed precision
-    and FP64; against the same problems stepped one after another through single-problem
-    contexts (mixed); per-problem relative l2 of the mixed result against the FP64 one."""
+def bench_batched(rbfsl, torch, stream, steps=10, seq_steps=3, P=64, Ns=(2562, 10242, 40962, 163842),
+                  precisions=("mixed", "fp64")):
+    """P independent local problems (N from Ns, (n, ell) from {(31,2), (55,3), (84,4)} with
+    r^(2 ell + 1), 1-16 tracers, own rotation or deformation), direct stencils, one persistent
+    fused kernel per step under a CUDA graph, in the given precisions; against the same problems
+    stepped one after another through single-problem contexts (mixed); per-problem relative l2
+    of the mixed result against the FP64 one."""
     from paper_1804_01609_gb300 import inputs
-    specs = inputs.batched_problems(64)
+    specs = inputs.batched_problems(P, Ns=Ns)
     probs = []
     for sp in specs:
         X = inputs.nodes(sp["N"], sp["seed"])
@@ -613,6 +614,8 @@ def bench_batched(rbfsl, torch, stream, steps=10, seq_steps=3):
     out = {"problems": len(probs), "nodes": nodes, "steps": steps}
     finals = {}
     for prec, name in ((rbfsl.MIXED, "mixed"), (rbfsl.FP64, "fp64")):
+        if name not in precisions:
+            continue
         b = rbfsl.Batch(0, stream=stream)
         ids = [b.add(X, q0, sp["n"], sp["ell"], sp["power"], sp["vel_kind"], sp["vel_params"], 1.0 / 100,
                      mode=rbfsl.DIRECT, precision=prec) for sp, X, q0 in probs]
@@ -650,12 +653,13 @@ def bench_batched(rbfsl, torch, stream, steps=10, seq_steps=3):
         torch.cuda.synchronize()
         seq_ms += e0.elapsed_time(e1) / seq_steps
         ctx.close()
-    d = [rel_l2(a, b) for a, b in zip(finals["mixed"], finals["fp64"])]
     out["sequential_contexts_mixed"] = {"ms_per_step": seq_ms, "value": nodes / (seq_ms / 1e3),
                                         "steps_timed_per_problem": seq_steps}
     out["batched_over_sequential"] = seq_ms / out["mixed"]["ms_per_step"]
-    out["accuracy_mixed_vs_fp64"] = {"steps": steps + 1, "rel_l2_max": float(max(d)),
-                                     "rel_l2_median": float(np.median(d))}
+    if "fp64" in finals:
+        d = [rel_l2(a, b) for a, b in zip(finals["mixed"], finals["fp64"])]
+        out["accuracy_mixed_vs_fp64"] = {"steps": steps + 1, "rel_l2_max": float(max(d)),
+                                         "rel_l2_median": float(np.median(d))}
     return out
 
 
@@ -834,7 +838,10 @@ def run_case(args):
         print(f"case wq: {json.dumps(r)}", flush=True)
         return
     if args.case == "batched":  # the batched leg alone
-        r = bench_batched(rbfsl, torch, torch.cuda.Stream())
+        st = torch.cuda.Stream()
+        r = bench_batched(rbfsl, torch, st)
+        r["small_problems_256"] = bench_batched(rbfsl, torch, st, steps=20, seq_steps=5, P=256, Ns=(642, 2562),
+                                                precisions=("mixed",))
         print(f"case batched: {json.dumps(json_safe(r))}", flush=True)
         return
     if args.case == "served":  # the served leg alone (--served-requests, --served-steps)
@@ -1072,6 +1079,9 @@ def main():
     batched = {}
     if not args.no_batched:
         batched = bench_batched(rbfsl, torch, stream)
+        # many small problems (N = 642 or 2,562), where single-problem steps are launch-bound
+        batched["small_problems_256"] = bench_batched(rbfsl, torch, stream, steps=20, seq_steps=5, P=256,
+                                                      Ns=(642, 2562), precisions=("mixed",))
     served = {}
     if not args.no_served:
         served = bench_served(rbfsl, R=args.served_requests, steps=tuple(args.served_steps))

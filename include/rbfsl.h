@@ -413,6 +413,9 @@ int rbfsl_batch_problem_stats(rbfsl_batch *b, int id, rbfsl_stats *out);
 int rbfsl_batch_set_graph(rbfsl_batch *b, int use_graph);
 /* Autotuner: for every RBFSL_DIRECT (n, ell) class of the batch, time the persistent kernel
  * with one warp per point and with four warps per point and keep the faster for later steps.
+ * Shapes whose block would need more than a quarter of an SM's shared memory (or more than
+ * the largest single-point block) are not tried: every block of the persistent kernel gets
+ * the largest class's shared memory, so such a shape would slow the other classes down.
  * Fields, times and step counts are unchanged. choices (may be NULL) receives triples
  * (n, ell, points per tile: 4 = one warp per point, 1 = four warps per point). */
 int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices);

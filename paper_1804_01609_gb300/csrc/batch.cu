@@ -110,7 +110,7 @@ __device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w
     }
 }
 
-__global__ void __launch_bounds__(128) batch_solve_kernel(const BatchDesc *__restrict__ d, int np,
+__global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__restrict__ d, int np,
                                                           int64_t total_tiles,
                                                           unsigned long long *__restrict__ counter) {
     extern __shared__ double sm[];
@@ -610,16 +610,26 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
     cudaEvent_t e0, e1;
     RBFSL_CUDA_TRY(cudaEventCreate(&e0));
     RBFSL_CUDA_TRY(cudaEventCreate(&e1));
+    // The persistent kernel's blocks all get the largest class's shared memory, so a tile shape
+    // timed alone can slow the other classes down: keep every class's block within a quarter of
+    // an SM's shared memory (four blocks per SM), or within the largest single-point block when
+    // that is bigger.
+    int max_smem = 0, sm_smem = 0;
+    RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device));
+    int block_cap = sm_smem / 4 - 1024;  // the runtime reserves 1 KB per block
+    for (long long key : classes) {
+        const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
+        block_cap = std::max(block_cap, batch_point_doubles(RBFSL_DIRECT, kn, km, (km + 1) | 1, knn_cap(kn)) * 8);
+    }
     int nout = 0;
     for (long long key : classes) {
         float best_ms = 1e30f;
-        int best = 4;
-        int max_smem = 0;
-        RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+        int best = 1;
         const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
         const int per_bytes = batch_point_doubles(RBFSL_DIRECT, kn, km, (km + 1) | 1, knn_cap(kn)) * 8;
         for (int ppt : {4, 1}) {
-            if (ppt == 4 && 4 * per_bytes > max_smem) continue;  // four points do not fit on chip
+            if (ppt == 4 && (4 * per_bytes > max_smem || 4 * per_bytes > block_cap)) continue;
             // only this class active, with the candidate tile shape
             std::vector<int> saved;
             for (auto &h : b->probs) {

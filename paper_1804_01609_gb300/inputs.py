@@ -283,14 +283,14 @@ def config_nl(N: int, ic: str = "cosine", method: str = "local", n: int = 31, el
                     steps=steps, dt=5.0 / steps, tracers=TracerSet([fn]), seed=seed)
 
 
-def batched_problems(P: int = 64, seed: int = SEED_BASE + 4):
-    """Descriptors of P independent local problems: N from {2562, 10242, 40962, 163842},
-    (n, ell) from {(31,2),(55,3),(84,4)}, 1..16 tracers, each with its own tilted rotation
-    or deformation field (seeded parameters)."""
+def batched_problems(P: int = 64, seed: int = SEED_BASE + 4, Ns=(2562, 10242, 40962, 163842)):
+    """Descriptors of P independent local problems: N from Ns, (n, ell) from
+    {(31,2),(55,3),(84,4)}, 1..16 tracers, each with its own tilted rotation or deformation
+    field (seeded parameters)."""
     rng = np.random.default_rng(seed)
     out = []
     for p in range(P):
-        N = int(rng.choice([2562, 10242, 40962, 163842]))
+        N = int(rng.choice(list(Ns)))
         n, ell = [(31, 2), (55, 3), (84, 4)][int(rng.integers(0, 3))]
         T = int(rng.integers(1, 17))
         if rng.random() < 0.5:
