@@ -471,6 +471,13 @@ int rbfsl_server_result(rbfsl_server *s, uint64_t ticket, double *q_out, rbfsl_r
 int rbfsl_server_wait_idle(rbfsl_server *s, double timeout_s);
 int rbfsl_server_info(rbfsl_server *s, rbfsl_server_info_t *out);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (2 flops per FMA): chains of
+ * dependent FMAs in every thread of 8 blocks of 256 threads per SM, `iters` FMAs per chain and
+ * eight chains per thread, timed with CUDA events after one shorter warm-up launch. The roofline
+ * denominator of the FP64 stencil solves. The paper has no counterpart: a measurement utility.
+ * Synchronises `stream`. Errors: EINVAL, ECUDA. */
+int rbfsl_fp64_fma_rate(int64_t iters, double *tflops, void *stream);
+
 /* Message of the last failed call on this context (thread-local when ctx is NULL). */
 const char *rbfsl_last_error(const rbfsl_ctx *ctx);
 const char *rbfsl_version(void);

@@ -55,6 +55,7 @@ class Stats(ctypes.Structure):
 
 SIGNATURES = {
     "rbfsl_version": (ctypes.c_char_p, []),
+    "rbfsl_fp64_fma_rate": (_I, [_I64, _P, _P]),
     "rbfsl_last_error": (ctypes.c_char_p, [_P]),
     "rbfsl_trace_rk4": (_I, [_P, _I64, _I, _P, _D, _D, _I, _P, _P]),
     "rbfsl_trace_rk5": (_I, [_P, _I64, _I, _P, _D, _D, _I, _P, _P]),
@@ -171,6 +172,13 @@ def _dtype_code(t):
 
 
 # --------------------------------------------------------------------------- stateless ops
+def rbfsl_fp64_fma_rate(iters=1 << 16, stream=None):
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    v = ctypes.c_double(0.0)
+    _check(load().rbfsl_fp64_fma_rate(iters, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
 def rbfsl_trace_rk4(x, vel_kind, vel_params, t1, dt, precision, xi, stream=None):
     prm = np.ascontiguousarray(vel_params, dtype=np.float64)
     _check(load().rbfsl_trace_rk4(_ptr(x), x.shape[0], vel_kind, prm.ctypes.data, t1, dt,
