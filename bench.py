@@ -339,7 +339,7 @@ def finite_or_none(v):
     return v if np.isfinite(v) else None
 
 
-def global_ctx(rbfsl, w, prec, stream, eps=None, form=None):
+def global_ctx(rbfsl, w, prec, stream, eps=None, form=None, evaluation=None):
     ctx = rbfsl.Context(0, stream=stream)
     ctx.set_nodes(w.X)
     ctx.set_velocity(w.vel_kind, w.vel_params)
@@ -348,6 +348,8 @@ def global_ctx(rbfsl, w, prec, stream, eps=None, form=None):
     ctx.set_precision(prec)
     if form is not None:
         ctx.set_global_form(form)
+    if evaluation is not None:
+        ctx.set_global_eval(evaluation)
     ctx.set_dt(w.dt)
     ctx.set_tracers(w.q0())
     return ctx
@@ -402,17 +404,20 @@ def bench_global_cardinal(rbfsl, torch, stream, flush, K=5, accuracy_eps=(6.0, 9
 
 def bench_global(rbfsl, torch, stream, flush, K=3, accuracy_eps=(6.0, 9.0, 24.0)):
     """Global Gaussian RBF, N = 10,242, 64 smooth tracers, tilted rotation: one-time FP64 LU,
-    then per step an FP64 solve and the evaluation at the departure points (FP64, or split TF32
-    on the tensor cores in mixed precision). Step times at the workload's eps = 6; errors after
-    one revolution (200 steps) against the exact solution (the initial field) for several eps:
-    at eps = 6 the interpolation matrix is numerically singular (smallest LU pivot ~1e-15) and
-    the FP64 iteration itself diverges; eps = 9 is accurate in FP64; eps = 24 is well
+    then per step an FP64 solve and the evaluation at the departure points: FP64; mixed with
+    split TF32 on the tensor cores (the default); mixed with FP64 kernel values and FP32-pair
+    sums. Step times at the workload's eps = 6; errors after one revolution (200 steps)
+    against the exact solution (the initial field) for several eps: at eps = 6 the
+    interpolation matrix is numerically singular (smallest LU pivot ~1e-15) and the FP64
+    iteration itself diverges (the oracle's too); eps = 9 is accurate in FP64; eps = 24 is well
     conditioned. A diverged run is reported as null."""
     from paper_1804_01609_gb300 import inputs
     w = inputs.config_global_rotation()
     out = {"eps": w.eps}
-    for prec, name in ((rbfsl.FP64, "fp64"), (rbfsl.MIXED, "mixed")):
-        ctx = global_ctx(rbfsl, w, prec, stream)
+    variants = ((rbfsl.FP64, "fp64", None), (rbfsl.MIXED, "mixed", rbfsl.GLOBAL_EVAL_TC),
+                (rbfsl.MIXED, "mixed_fp32_pairs", rbfsl.GLOBAL_EVAL_PAIRS))
+    for prec, name, ev in variants:
+        ctx = global_ctx(rbfsl, w, prec, stream, evaluation=ev)
         t0 = time.perf_counter()
         ctx.step(1)
         torch.cuda.synchronize()
@@ -426,16 +431,17 @@ def bench_global(rbfsl, torch, stream, flush, K=3, accuracy_eps=(6.0, 9.0, 24.0)
     for eps in accuracy_eps:
         row = {"eps": eps}
         qs = {}
-        for prec, name in ((rbfsl.FP64, "fp64"), (rbfsl.MIXED, "mixed")):
-            ctx = global_ctx(rbfsl, w, prec, stream, eps)
+        for prec, name, ev in variants:
+            ctx = global_ctx(rbfsl, w, prec, stream, eps, evaluation=ev)
             ctx.step(w.steps)
             qs[name] = ctx.get_q()
             ctx.close()
             ok = bool(np.isfinite(qs[name]).all())
             row[name + "_l2_vs_exact"] = finite_or_none(rel_l2(qs[name], q0)) if ok else None
-        if row["fp64_l2_vs_exact"] is not None and row["mixed_l2_vs_exact"] is not None:
-            row["mixed_over_fp64"] = row["mixed_l2_vs_exact"] / row["fp64_l2_vs_exact"]
-            row["mixed_l2_vs_fp64"] = finite_or_none(rel_l2(qs["mixed"], qs["fp64"]))
+        for name in ("mixed", "mixed_fp32_pairs"):
+            if row["fp64_l2_vs_exact"] is not None and row[name + "_l2_vs_exact"] is not None:
+                row[name + "_over_fp64"] = row[name + "_l2_vs_exact"] / row["fp64_l2_vs_exact"]
+                row[name + "_l2_vs_fp64"] = finite_or_none(rel_l2(qs[name], qs["fp64"]))
         acc.append(row)
     out["accuracy_after_200_steps"] = acc
     return out
@@ -466,6 +472,11 @@ def bench_global_eval(rbfsl, torch, stream, flush, K=10):
                   stream, flush, torch)
     t64 = time_op(lambda: rbfsl.rbfsl_global_eval(xi, x, rbfsl.GAUSS, w.eps, C, o64, stream=stream), 3,
                   stream, flush, torch)
+    with torch.cuda.stream(stream):
+        o_pr = torch.empty((N, T, 2), dtype=torch.float32, device="cuda")
+    ws_pr = rbfsl.rbfsl_global_eval_pairs(xi, x, rbfsl.GAUSS, w.eps, C, o_pr, stream=stream)
+    t_pr = time_op(lambda: rbfsl.rbfsl_global_eval_pairs(xi, x, rbfsl.GAUSS, w.eps, C, o_pr, workspace=ws_pr,
+                                                         stream=stream), K, stream, flush, torch)
     torch.cuda.synchronize()
     scale = float(o64.abs().max())
     flop = 2.0 * N * N * T
@@ -476,7 +487,11 @@ def bench_global_eval(rbfsl, torch, stream, flush, K=10):
                              "max_err_vs_fp64_rel_to_max": float((o_tc.double() - o64).abs().max()) / scale},
             "fp32_cuda_cores": {"us": 1e3 * t32, "useful_tflops": flop / (t32 * 1e-3) / 1e12,
                                 "max_err_vs_fp64_rel_to_max": float((o32.double() - o64).abs().max()) / scale},
-            "fp64": {"us": 1e3 * t64, "useful_tflops": flop / (t64 * 1e-3) / 1e12}}
+            "fp64": {"us": 1e3 * t64, "useful_tflops": flop / (t64 * 1e-3) / 1e12},
+            "fp32_pairs": {"kernel": "phi_pairs_kernel + cardinal_apply_pair_kernel (FP64 kernel values, pair sums)",
+                           "us": 1e3 * t_pr, "useful_tflops": flop / (t_pr * 1e-3) / 1e12,
+                           "max_err_vs_fp64_rel_to_max": float(((o_pr[..., 0].double() + o_pr[..., 1].double())
+                                                                - o64).abs().max()) / scale}}
 
 
 # ----------------------------------------------------------------------------- paper cases

@@ -263,6 +263,19 @@ int rbfsl_pu_apply(rbfsl_pu *pu, const double *q, int T, const double *p, int64_
  * status: device int32 or NULL; set to RBFSL_ETIMEDOUT if a bounded wait inside the kernel gave
  * up (out is then unspecified), otherwise left unchanged. Asynchronous on `stream`.
  * Errors: EINVAL (sizes, kernel, dtype, workspace too small or misaligned), ECUDA. */
+/* Global-interpolant evaluation to FP64 accuracy without FP64 products: Phi(p, x) formed in
+ * FP64 (the kernel and distance arithmetic of rbfsl_global_eval) and stored as FP32 pairs, the
+ * coefficients split into pairs, then out = Phi c by FP32-pair arithmetic (the product of
+ * rbfsl_cardinal_apply): ~2^-48 relative per term. c: device N x T FP64; out: device Nq x T
+ * FP32 pairs (Nq x T x 2 floats). workspace: device, 256-byte aligned, at least
+ * rbfsl_global_eval_pairs_workspace_bytes(Nq, N, T) (Nq x N x 8 bytes for Phi, the split
+ * coefficients and the product's split-K partials); owned by the caller, not shared between
+ * calls that overlap on the GPU. Asynchronous on `stream`. Errors: EINVAL, ECUDA. */
+size_t rbfsl_global_eval_pairs_workspace_bytes(int64_t Nq, int64_t N, int T);
+int rbfsl_global_eval_pairs(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
+                            double eps, const double *c, int T, void *out, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 size_t rbfsl_global_eval_tc_workspace_bytes(int64_t Nq, int64_t N, int T);
 int rbfsl_global_eval_tc(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
                          double eps, const void *c, int c_dtype, int T, float *out,
@@ -356,6 +369,16 @@ int rbfsl_set_integrator(rbfsl_ctx *ctx, int order);
  * depends on the departure points). Errors: EINVAL. */
 enum { RBFSL_GLOBAL_SOLVE = 0, RBFSL_GLOBAL_CARDINAL = 1 };
 int rbfsl_set_global_form(rbfsl_ctx *ctx, int form);
+/* Evaluation arithmetic of the RBFSL_GLOBAL_SOLVE step in RBFSL_MIXED (the solve is FP64 in
+ * both). RBFSL_GLOBAL_EVAL_TC (default): split-TF32 products on the tensor cores
+ * (rbfsl_global_eval_tc; fastest, ~2^-22 relative). RBFSL_GLOBAL_EVAL_PAIRS: kernel values in
+ * FP64, the sum Phi(Xi, X) C in FP32 pairs (rbfsl_global_eval_pairs; ~2^-48 relative, an N x N
+ * pair workspace). Where the interpolation matrix is ill-conditioned the iteration feeds the
+ * evaluation's rounding back through the next solve, so neither matches FP64 there (at Gaussian
+ * eps = 9 on 10,242 nodes both diverge while FP64 does not); the cardinal form does.
+ * Invalidates prepared state. Errors: EINVAL. */
+enum { RBFSL_GLOBAL_EVAL_PAIRS = 0, RBFSL_GLOBAL_EVAL_TC = 1 };
+int rbfsl_set_global_eval(rbfsl_ctx *ctx, int kind);
 int rbfsl_set_time(rbfsl_ctx *ctx, double t);
 /* Initial field q(X, t): N x T, element type dtype (converted to the context precision),
  * on the host (copied synchronously) or the device (copied on the context stream).

@@ -74,6 +74,7 @@ struct rbfsl_ctx {
     double dt = 0.0, t = 0.0;
     int integrator = RBFSL_RK4;
     int global_form = RBFSL_GLOBAL_SOLVE;
+    int global_eval = RBFSL_GLOBAL_EVAL_TC;  // mixed precision: evaluation arithmetic
     int T = 0;
     void *q = nullptr, *q_next = nullptr;  // N x T, FP64 or FP32 pairs (mixed), 8 bytes each
     int64_t steps_done = 0;
@@ -214,7 +215,8 @@ int prepare_global(rbfsl_ctx *c) {
     CTX_TRY(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int32_t), c->stream));
     if (c->precision == RBFSL_MIXED) {
         if ((rc = dalloc(c, &c->Q64, N * T * sizeof(double)))) return rc;
-        c->tc_ws_bytes = global_eval_tc_workspace(N, N, (int)T);
+        c->tc_ws_bytes = c->global_eval == RBFSL_GLOBAL_EVAL_TC ? global_eval_tc_workspace(N, N, (int)T)
+                                                                 : global_eval_pairs_workspace(N, N, (int)T);
         if ((rc = dalloc(c, &c->tc_ws, c->tc_ws_bytes))) return rc;
     }
     if ((rc = factor_global(c))) return rc;
@@ -270,6 +272,13 @@ int one_step_global(rbfsl_ctx *c) {
         CTX_RC(c, global_solve(c->LU, c->perm, N, (const double *)c->q, c->T, c->C64, c->stream));
         CTX_RC(c, launch_global_eval(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T, RBFSL_F64,
                                      c->q_next, RBFSL_F64, c->stream));
+    } else if (c->global_eval == RBFSL_GLOBAL_EVAL_PAIRS) {
+        // FP64 solve of the field (FP32 pairs widened); kernel values in FP64, the sum in
+        // FP32-pair arithmetic, straight into the pair field
+        from_pair_kernel<double><<<blocks, 256, 0, c->stream>>>((const float2 *)c->q, c->Q64, NT);
+        CTX_RC(c, global_solve(c->LU, c->perm, N, c->Q64, c->T, c->C64, c->stream));
+        CTX_RC(c, launch_global_eval_pairs(c->xi, N, c->X, N, c->kkind, c->kparam, c->C64, c->T,
+                                           (float2 *)c->q_next, c->tc_ws, c->tc_ws_bytes, c->stream));
     } else {
         // FP64 solve of the field (FP32 pairs widened); evaluation on the tensor cores (split
         // TF32, FP32 accumulation) into the freed FP64 right-hand side buffer, stored as pairs
@@ -599,6 +608,19 @@ int rbfsl_set_global_form(rbfsl_ctx *c, int form) {
         release_prepared(c);
     }
     c->global_form = form;
+    return RBFSL_OK;
+}
+
+int rbfsl_set_global_eval(rbfsl_ctx *c, int kind) {
+    if (!c) return fail(nullptr, RBFSL_EINVAL, "null context");
+    if (kind != RBFSL_GLOBAL_EVAL_PAIRS && kind != RBFSL_GLOBAL_EVAL_TC)
+        return fail(c, RBFSL_EINVAL, "global evaluation must be RBFSL_GLOBAL_EVAL_PAIRS or RBFSL_GLOBAL_EVAL_TC");
+    if (kind != c->global_eval && c->method == RBFSL_GLOBAL) {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        release_prepared(c);
+    }
+    c->global_eval = kind;
     return RBFSL_OK;
 }
 

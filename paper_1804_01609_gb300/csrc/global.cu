@@ -676,6 +676,74 @@ extern "C" int rbfsl_global_eval(const double *p, int64_t Nq, const double *x, i
 }
 
 // ---------------------------------------------------------------------------------------
+// FP64-accurate evaluation without FP64 products: the kernel matrix Phi(P, X) formed in FP64
+// (the same radial function and distance operations as the FP64 evaluation) and stored as FP32
+// pairs, the coefficients split into pairs, then Phi C by the FP32-pair product of the cardinal
+// form (rbfsl_cardinal_apply): ~2^-48 relative per term against the split-TF32 evaluation's
+// ~2^-22, at a fraction of the FP64 products' cost.
+namespace rbfsl {
+
+__global__ void phi_pairs_kernel(const double *__restrict__ P, int64_t Nq, const double *__restrict__ X, int64_t N,
+                                 int kind, double eps2, float2 *__restrict__ E) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= Nq * N) return;
+    const int64_t i = e / N, j = e - i * N;
+    const double dx = P[3 * i] - X[3 * j], dy = P[3 * i + 1] - X[3 * j + 1], dz = P[3 * i + 2] - X[3 * j + 2];
+    E[e] = pair_from(radial(kind, eps2, dx * dx + dy * dy + dz * dz));
+}
+
+__global__ void f64_to_pairs(const double *__restrict__ in, float2 *__restrict__ out, int64_t n) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) out[e] = pair_from(in[e]);
+}
+
+size_t global_eval_pairs_workspace(int64_t Nq, int64_t N, int T) {
+    const size_t phi = ((size_t)Nq * N * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t cp = ((size_t)N * T * sizeof(float2) + 255) & ~(size_t)255;
+    return phi + cp + cardinal_apply_workspace(Nq, N, T);
+}
+
+int launch_global_eval_pairs(const double *P, int64_t Nq, const double *X, int64_t N, int kind, double eps,
+                             const double *C, int T, float2 *out, void *ws, size_t ws_bytes, cudaStream_t s) {
+    if (Nq == 0) return RBFSL_OK;
+    const size_t need = global_eval_pairs_workspace(Nq, N, T);
+    if (!ws || ws_bytes < need) {
+        set_error("global_eval_pairs: workspace too small");
+        return RBFSL_EINVAL;
+    }
+    float2 *E = (float2 *)ws;
+    const size_t phi = ((size_t)Nq * N * sizeof(float2) + 255) & ~(size_t)255;
+    float2 *Cp = (float2 *)((char *)ws + phi);
+    const size_t cp = ((size_t)N * T * sizeof(float2) + 255) & ~(size_t)255;
+    void *aws = (char *)ws + phi + cp;
+    const int64_t ne = Nq * N, nc = N * (int64_t)T;
+    phi_pairs_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(P, Nq, X, N, kind, eps * eps, E);
+    f64_to_pairs<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(C, Cp, nc);
+    int rc = launch_status("global_eval_pairs");
+    if (rc) return rc;
+    return launch_cardinal_apply(E, Nq, N, Cp, T, RBFSL_F32X2, out, aws, ws_bytes - phi - cp, s);
+}
+
+}  // namespace rbfsl
+
+extern "C" size_t rbfsl_global_eval_pairs_workspace_bytes(int64_t Nq, int64_t N, int T) {
+    if (Nq < 0 || N < 1 || T < 1) return 0;
+    return rbfsl::global_eval_pairs_workspace(Nq, N, T);
+}
+
+extern "C" int rbfsl_global_eval_pairs(const double *p, int64_t Nq, const double *x, int64_t N, int kernel,
+                                       double eps, const double *c, int T, void *out, void *workspace,
+                                       size_t workspace_bytes, void *stream) {
+    using namespace rbfsl;
+    RBFSL_CHECK_ARG(Nq >= 0 && N >= 1 && T >= 1, "global_eval_pairs: bad sizes");
+    RBFSL_CHECK_ARG(Nq == 0 || (p && x && c && out && workspace), "global_eval_pairs: null pointer");
+    RBFSL_CHECK_ARG((kernel == RBFSL_GAUSS || kernel == RBFSL_IMQ) && eps > 0, "global_eval_pairs: bad kernel");
+    RBFSL_CHECK_ARG(((uintptr_t)workspace & 255) == 0, "global_eval_pairs: workspace must be 256-byte aligned");
+    return launch_global_eval_pairs(p, Nq, x, N, kernel, eps, c, T, (float2 *)out, workspace, workspace_bytes,
+                                    (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------------------
 // Allocation-free variant of rbfsl_global_factor (no counterpart in the paper).
 //
 // Some callers cannot call cudaMalloc at the point where they factorise: a serving process

@@ -116,6 +116,10 @@ int launch_global_eval_tc(const double *P, int64_t Nq, const double *X, int64_t 
                           const void *C, int c_dtype, int T, float *out, void *workspace, int32_t *status,
                           cudaStream_t s);
 
+size_t global_eval_pairs_workspace(int64_t Nq, int64_t N, int T);
+int launch_global_eval_pairs(const double *P, int64_t Nq, const double *X, int64_t N, int kind, double eps,
+                             const double *C, int T, float2 *out, void *ws, size_t ws_bytes, cudaStream_t s);
+
 int global_cardinal_build(const double *LU, const int32_t *perm, const double *X, int64_t N, int kind,
                           double eps, const double *P, int64_t Nq, void *E, int e_dtype, cudaStream_t s);
 size_t cardinal_apply_workspace(int64_t Nq, int64_t N, int T);

@@ -23,6 +23,7 @@ PHS, GAUSS, IMQ = 0, 1, 2
 FP64, MIXED = 0, 1
 RK4, RK5 = 4, 5
 GLOBAL_SOLVE, GLOBAL_CARDINAL = 0, 1
+GLOBAL_EVAL_PAIRS, GLOBAL_EVAL_TC = 0, 1
 F64, F32, F32X2 = 0, 1, 2
 HOST, DEVICE = 0, 1
 PU_WENDLAND, PU_BSPLINE = 0, 1
@@ -76,6 +77,9 @@ SIGNATURES = {
     "rbfsl_cardinal_apply_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
     "rbfsl_cardinal_apply": (_I, [_P, _I64, _I64, _P, _I, _I, _P, _P, ctypes.c_size_t, _P]),
     "rbfsl_set_global_form": (_I, [_P, _I]),
+    "rbfsl_set_global_eval": (_I, [_P, _I]),
+    "rbfsl_global_eval_pairs_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I]),
+    "rbfsl_global_eval_pairs": (_I, [_P, _I64, _P, _I64, _I, _D, _P, _I, _P, _P, ctypes.c_size_t, _P]),
     "rbfsl_pu_create": (_I, [_P, _P, _I64, _P, _I64, _D, _I, _I, _D, _P]),
     "rbfsl_pu_destroy": (_I, [_P]),
     "rbfsl_pu_apply": (_I, [_P, _P, _I, _P, _I64, _I, _I, _P, _P, _P]),
@@ -486,6 +490,20 @@ def rbfsl_global_eval_tc(p, x, kernel, eps, c, out, workspace=None, status=None,
     return workspace
 
 
+def rbfsl_global_eval_pairs(p, x, kernel, eps, c, out, workspace=None, stream=None):
+    """FP64-accurate evaluation in FP32-pair arithmetic; c: FP64 N x T; out: float32 Nq x T x 2;
+    workspace: a uint8 device tensor (allocated here when None, 256-byte aligned)."""
+    import torch
+    T = c.shape[1] if c.dim() == 2 else 1
+    need = load().rbfsl_global_eval_pairs_workspace_bytes(p.shape[0], x.shape[0], T)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=c.device)
+    _check(load().rbfsl_global_eval_pairs(_ptr(p), p.shape[0], _ptr(x), x.shape[0], kernel, float(eps),
+                                          _ptr(c), T, _ptr(out), _ptr(workspace), workspace.numel(),
+                                          _stream(stream)))
+    return workspace
+
+
 def _f64_or_pairs(t):
     import torch
     if t.dtype == torch.float64:
@@ -584,6 +602,9 @@ class Context:
 
     def set_global_form(self, form):
         self._c(load().rbfsl_set_global_form(self._h, form))
+
+    def set_global_eval(self, kind):
+        self._c(load().rbfsl_set_global_eval(self._h, kind))
 
     def set_time(self, t):
         self._c(load().rbfsl_set_time(self._h, float(t)))
