@@ -534,9 +534,14 @@ def bench_paper_cases(rbfsl, torch, stream, Ns=(2562, 10242, 40962, 92162)):
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         q = ctx.get_q()[:, 0]
+        st = ctx.get_stats()
         ctx.close()
         m = diagnostics.error_measures(q, w.q0()[:, 0])
         m.update({"N": w.N, "steps_s": secs * w.steps / max(w.steps - 1, 1)})
+        if method == "pu":
+            # departure points in no patch (the patches must cover the sphere, Sec. 2.3):
+            # their values are NaN and flagged, so the error measures are then undefined
+            m["uncovered_points"] = int(st.uncovered_points)
         return m
 
     def sweep(mk, method, mode, ns, Nlist):
