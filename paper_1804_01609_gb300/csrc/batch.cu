@@ -2,10 +2,14 @@
 // velocity, tracers, precision, stencil mode) advanced together, one SL step (Algorithm 1)
 // per graph replay:
 //   1. batch_trace_kernel     departure points of every node of every active problem;
-//   2. batch_solve_kernel     ONE persistent fused kernel: blocks take tiles of points from a
-//                             shared counter; per point the k-NN stencil, the FP64 weights
-//                             (direct solve or stored centre-stencil LU) and the gather-dot
-//                             into the next field, with stencil and weights kept on chip;
+//   2. batch_solve_kernel     one persistent fused kernel per stencil class (mode, n, ell),
+//                             the classes on parallel graph branches: blocks take tiles of the
+//                             class's points from its counter; per point the k-NN stencil, the
+//                             FP64 weights (direct solve or stored centre-stencil LU) and the
+//                             gather-dot into the next field, with stencil and weights kept on
+//                             chip. Each class's launch has its own block shared memory and
+//                             grid, so a small class is not held to the largest class's
+//                             occupancy;
 //   3. batch_finalize_kernel  per-problem failure counters, time and step advance, counter
 //                             reset.
 // The per-point arithmetic is the same device code as the single-problem kernels
@@ -110,8 +114,9 @@ __device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w
     }
 }
 
-__global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__restrict__ d, int np,
-                                                          int64_t total_tiles,
+// Tiles [tile_begin, tile_end) of the table's problems [p_begin, p_begin + np) (one class).
+__global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__restrict__ d, int p_begin, int np,
+                                                          int64_t tile_begin, int64_t tile_end,
                                                           unsigned long long *__restrict__ counter) {
     extern __shared__ double sm[];
     __shared__ long long s_tile;
@@ -119,10 +124,10 @@ __global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__
     for (;;) {
         if (t == 0) s_tile = (long long)atomicAdd(counter, 1ULL);
         __syncthreads();
-        const int64_t tile = s_tile;
+        const int64_t tile = tile_begin + s_tile;
         __syncthreads();
-        if (tile >= total_tiles) break;
-        const int p = find_problem(d, np, tile, true);
+        if (tile >= tile_end) break;
+        const int p = p_begin + find_problem(d + p_begin, np, tile, true);
         const BatchDesc &b = d[p];
         if (!b.active) continue;
         const int n = b.n, m = b.m, ld = b.ld, cap = knn_cap(b.mode == RBFSL_DIRECT ? n : 1);
@@ -209,14 +214,24 @@ __global__ void batch_count_kernel(BatchDesc *__restrict__ d, int np, int64_t to
     else if (s == RBFSL_EKNN) atomicAdd(&b.ctr[1], 1ULL);
 }
 
-__global__ void batch_finalize_kernel(BatchDesc *__restrict__ d, int np, unsigned long long *__restrict__ counter) {
+__global__ void batch_finalize_kernel(BatchDesc *__restrict__ d, int np, unsigned long long *__restrict__ counters,
+                                      int nc) {
     for (int p = threadIdx.x; p < np; p += blockDim.x) {
         if (!d[p].active) continue;
         d[p].t = d[p].t + d[p].dt;
         d[p].step += 1;
     }
-    if (threadIdx.x == 0) *counter = 0ULL;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) counters[c] = 0ULL;
 }
+
+// One persistent launch per stencil class: its table range, tile range and launch shape.
+struct ClassLaunch {
+    int p0 = 0, np = 0;
+    int64_t t0 = 0, t1 = 0;
+    int smem = 0, grid = 0;
+    long long key = 0;
+};
+constexpr int kMaxClasses = 64;  // class counters allocated with the batch
 
 struct HostProblem {
     bool used = false;
@@ -237,11 +252,14 @@ struct rbfsl_batch {
     std::vector<rbfsl::HostProblem> probs;
     rbfsl::BatchDesc *d_table = nullptr;
     int table_cap = 0;
-    unsigned long long *d_counter = nullptr;
-    int np = 0;                    // slots in the device table (compacted active problems)
+    unsigned long long *d_counter = nullptr;  // kMaxClasses tile counters, one per class
+    int np = 0;                    // slots in the device table (used problems, grouped by class)
     std::vector<int> slot_of;      // problem id -> table slot (-1 if not in the table)
     int64_t total_nodes = 0, total_tiles = 0;
-    int smem = 0, grid = 0;
+    std::vector<rbfsl::ClassLaunch> classes;
+    std::vector<cudaStream_t> side;      // class c > 0 runs on side[c - 1] (fork / join by events)
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork = nullptr;
     bool dirty = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -254,6 +272,7 @@ namespace rbfsl {
 namespace {
 
 long long class_key(int n, int ell) { return (long long)n * 64 + ell; }
+long long group_key(const BatchDesc &d) { return (long long)d.mode * 1000000 + class_key(d.n, d.ell); }
 
 int default_ppt(const rbfsl_batch *b, int n, int ell, int mode) {
     if (mode == RBFSL_CENTER) return 4;
@@ -270,27 +289,53 @@ void free_problem(HostProblem &h) {
     h = HostProblem();
 }
 
-// Rebuild the device table (active problems in id order), prefix offsets, launch shape.
+// Rebuild the device table (used problems grouped by stencil class, in id order within a
+// class), prefix offsets, and each class's launch shape.
 int rebuild(rbfsl_batch *b) {
     std::vector<BatchDesc> tab;
     b->slot_of.assign(b->probs.size(), -1);
+    b->classes.clear();
+    std::vector<long long> keys;
+    for (auto &h : b->probs)
+        if (h.used && std::find(keys.begin(), keys.end(), group_key(h.d)) == keys.end()) keys.push_back(group_key(h.d));
+    std::sort(keys.begin(), keys.end());
+    if ((int)keys.size() > kMaxClasses) {
+        set_error("batch: more than 64 stencil classes");
+        return RBFSL_EINVAL;
+    }
     int64_t nodes = 0, tiles = 0;
-    int smem = 0;
-    for (size_t id = 0; id < b->probs.size(); ++id) {
-        HostProblem &h = b->probs[id];
-        if (!h.used) continue;
-        BatchDesc d = h.d;
-        d.ppt = default_ppt(b, d.n, d.ell, d.mode);
-        h.d.ppt = d.ppt;
-        d.node0 = nodes;
-        d.tile0 = tiles;
-        nodes += d.N;
-        tiles += d.ppt == 4 ? (d.N + 3) / 4 : d.N;
-        const int cap = knn_cap(d.mode == RBFSL_DIRECT ? d.n : 1);
-        const int per = batch_point_doubles(d.mode, d.n, d.m, d.ld, cap) * 8;
-        smem = std::max(smem, d.ppt == 4 ? 4 * per : per);
-        b->slot_of[id] = (int)tab.size();
-        tab.push_back(d);
+    int max_smem = 0, sms = 0;
+    RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    for (long long key : keys) {
+        ClassLaunch cl;
+        cl.key = key;
+        cl.p0 = (int)tab.size();
+        cl.t0 = tiles;
+        for (size_t id = 0; id < b->probs.size(); ++id) {
+            HostProblem &h = b->probs[id];
+            if (!h.used || group_key(h.d) != key) continue;
+            BatchDesc d = h.d;
+            d.ppt = default_ppt(b, d.n, d.ell, d.mode);
+            h.d.ppt = d.ppt;
+            d.node0 = nodes;
+            d.tile0 = tiles;
+            nodes += d.N;
+            tiles += d.ppt == 4 ? (d.N + 3) / 4 : d.N;
+            const int cap = knn_cap(d.mode == RBFSL_DIRECT ? d.n : 1);
+            const int per = batch_point_doubles(d.mode, d.n, d.m, d.ld, cap) * 8;
+            cl.smem = std::max(cl.smem, d.ppt == 4 ? 4 * per : per);
+            b->slot_of[id] = (int)tab.size();
+            tab.push_back(d);
+        }
+        cl.np = (int)tab.size() - cl.p0;
+        cl.t1 = tiles;
+        if (cl.smem > max_smem) {
+            set_error("batch: a problem's per-block shared memory (" + std::to_string(cl.smem) +
+                      " bytes) exceeds the device limit");
+            return RBFSL_EINVAL;
+        }
+        b->classes.push_back(cl);
     }
     if ((int)tab.size() > b->table_cap) {
         cudaFree(b->d_table);
@@ -309,34 +354,59 @@ int rebuild(rbfsl_batch *b) {
     b->np = (int)tab.size();
     b->total_nodes = nodes;
     b->total_tiles = tiles;
-    b->smem = smem;
-    if (smem > 0) {
-        int max_smem = 0;
-        RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-        if (smem > max_smem) {
-            set_error("batch: a problem's per-block shared memory (" + std::to_string(smem) +
-                      " bytes) exceeds the device limit");
-            return RBFSL_EINVAL;
+    int smem_set = 0;
+    for (auto &cl : b->classes) {
+        if (cl.smem > smem_set) {  // the attribute is per kernel: the largest class's size
+            RBFSL_CUDA_TRY(cudaFuncSetAttribute(batch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cl.smem));
+            smem_set = cl.smem;
         }
-        RBFSL_CUDA_TRY(cudaFuncSetAttribute(batch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int per_sm = 0, sms = 0;
-        RBFSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel, 128, smem));
-        RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-        b->grid = std::max(1, per_sm) * sms;
     }
+    for (auto &cl : b->classes) {
+        int per_sm = 0;
+        RBFSL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_solve_kernel, 128, cl.smem));
+        const int64_t g = (int64_t)std::max(1, per_sm) * sms;
+        cl.grid = (int)std::max<int64_t>(1, std::min<int64_t>(g, cl.t1 - cl.t0));
+    }
+    while (b->side.size() + 1 < b->classes.size()) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        RBFSL_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaStreamDestroy(st);
+            return launch_status("batch: event creation");
+        }
+        b->side.push_back(st);
+        b->side_done.push_back(ev);
+    }
+    if (!b->fork) RBFSL_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->dirty = false;
     return RBFSL_OK;
 }
 
+void launch_class(rbfsl_batch *b, int c, cudaStream_t s) {
+    const ClassLaunch &cl = b->classes[c];
+    batch_solve_kernel<<<cl.grid, 128, cl.smem, s>>>(b->d_table, cl.p0, cl.np, cl.t0, cl.t1, b->d_counter + c);
+}
+
 int enqueue_step(rbfsl_batch *b) {
     if (b->np == 0) return RBFSL_OK;
     const unsigned tb = (unsigned)((b->total_nodes + 255) / 256);
     batch_trace_kernel<<<tb, 256, 0, b->stream>>>(b->d_table, b->np, b->total_nodes);
-    batch_solve_kernel<<<b->grid, 128, b->smem, b->stream>>>(b->d_table, b->np, b->total_tiles, b->d_counter);
+    const int nc = (int)b->classes.size();
+    if (nc > 1) {  // classes 1.. on side streams, forked from and joined back into the stream
+        RBFSL_CUDA_TRY(cudaEventRecord(b->fork, b->stream));
+        for (int c = 1; c < nc; ++c) {
+            RBFSL_CUDA_TRY(cudaStreamWaitEvent(b->side[c - 1], b->fork, 0));
+            launch_class(b, c, b->side[c - 1]);
+            RBFSL_CUDA_TRY(cudaEventRecord(b->side_done[c - 1], b->side[c - 1]));
+        }
+    }
+    if (nc > 0) launch_class(b, 0, b->stream);
+    for (int c = 1; c < nc; ++c) RBFSL_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->side_done[c - 1], 0));
     batch_count_kernel<<<tb, 256, 0, b->stream>>>(b->d_table, b->np, b->total_nodes);
-    batch_finalize_kernel<<<1, 256, 0, b->stream>>>(b->d_table, b->np, b->d_counter);
+    batch_finalize_kernel<<<1, 256, 0, b->stream>>>(b->d_table, b->np, b->d_counter, nc);
     return launch_status("batch step");
 }
 
@@ -373,13 +443,13 @@ int rbfsl_batch_create(rbfsl_batch **out, int device, void *stream) {
     auto *b = new rbfsl_batch();
     b->device = device;
     b->stream = (cudaStream_t)stream;
-    if (cudaMalloc(&b->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc(&b->d_counter, kMaxClasses * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         delete b;
         set_error("batch_create: out of device memory");
         return RBFSL_ENOMEM;
     }
-    RBFSL_CUDA_TRY(cudaMemset(b->d_counter, 0, sizeof(unsigned long long)));
+    RBFSL_CUDA_TRY(cudaMemset(b->d_counter, 0, kMaxClasses * sizeof(unsigned long long)));
     *out = b;
     return RBFSL_OK;
 }
@@ -393,6 +463,9 @@ int rbfsl_batch_destroy(rbfsl_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_table);
     cudaFree(b->d_counter);
+    for (auto st : b->side) cudaStreamDestroy(st);
+    for (auto ev : b->side_done) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
     return RBFSL_OK;
 }
@@ -610,18 +683,8 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
     cudaEvent_t e0, e1;
     RBFSL_CUDA_TRY(cudaEventCreate(&e0));
     RBFSL_CUDA_TRY(cudaEventCreate(&e1));
-    // The persistent kernel's blocks all get the largest class's shared memory, so a tile shape
-    // timed alone can slow the other classes down: keep every class's block within a quarter of
-    // an SM's shared memory (four blocks per SM), or within the largest single-point block when
-    // that is bigger.
-    int max_smem = 0, sm_smem = 0;
+    int max_smem = 0;
     RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-    RBFSL_CUDA_TRY(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device));
-    int block_cap = sm_smem / 4 - 1024;  // the runtime reserves 1 KB per block
-    for (long long key : classes) {
-        const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
-        block_cap = std::max(block_cap, batch_point_doubles(RBFSL_DIRECT, kn, km, (km + 1) | 1, knn_cap(kn)) * 8);
-    }
     int nout = 0;
     for (long long key : classes) {
         float best_ms = 1e30f;
@@ -629,7 +692,7 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
         const int kn = (int)(key / 64), kell = (int)(key % 64), km = kn + (kell + 1) * (kell + 1);
         const int per_bytes = batch_point_doubles(RBFSL_DIRECT, kn, km, (km + 1) | 1, knn_cap(kn)) * 8;
         for (int ppt : {4, 1}) {
-            if (ppt == 4 && (4 * per_bytes > max_smem || 4 * per_bytes > block_cap)) continue;
+            if (ppt == 4 && 4 * per_bytes > max_smem) continue;
             // only this class active, with the candidate tile shape
             std::vector<int> saved;
             for (auto &h : b->probs) {
@@ -638,15 +701,18 @@ int rbfsl_batch_autotune(rbfsl_batch *b, int *choices, int max_choices) {
             }
             b->tile_rule[key] = ppt;
             if ((rc = rebuild(b))) break;
+            int c = 0;
+            while (c < (int)b->classes.size() && b->classes[c].key != (long long)RBFSL_DIRECT * 1000000 + key) ++c;
+            if (c == (int)b->classes.size()) { rc = RBFSL_EINVAL; set_error("batch_autotune: class not found"); break; }
             const unsigned tb = (unsigned)((b->total_nodes + 255) / 256);
             batch_trace_kernel<<<tb, 256, 0, b->stream>>>(b->d_table, b->np, b->total_nodes);
-            cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream);
-            batch_solve_kernel<<<b->grid, 128, b->smem, b->stream>>>(b->d_table, b->np, b->total_tiles, b->d_counter);
-            cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream);
+            cudaMemsetAsync(b->d_counter + c, 0, sizeof(unsigned long long), b->stream);
+            launch_class(b, c, b->stream);
+            cudaMemsetAsync(b->d_counter + c, 0, sizeof(unsigned long long), b->stream);
             cudaEventRecord(e0, b->stream);
-            batch_solve_kernel<<<b->grid, 128, b->smem, b->stream>>>(b->d_table, b->np, b->total_tiles, b->d_counter);
+            launch_class(b, c, b->stream);
             cudaEventRecord(e1, b->stream);
-            cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream);
+            cudaMemsetAsync(b->d_counter + c, 0, sizeof(unsigned long long), b->stream);
             if ((rc = launch_status("batch_autotune"))) break;
             RBFSL_CUDA_TRY(cudaEventSynchronize(e1));
             float ms = 0.f;
