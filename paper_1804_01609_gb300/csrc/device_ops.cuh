@@ -367,13 +367,21 @@ __host__ __device__ inline int knn_cap(int k) {
 // interchanges): m^3 / 6 FMAs instead of elimination's m^3 / 3, on the lower triangle only.
 // The PHS block has a zero diagonal, so the first pivots are 2 x 2.
 //
+// Blocked form (delayed trailing updates, LAPACK's panel scheme for the symmetric indefinite
+// factorisation): the pivot columns of a panel of up to kPanel columns are updated on the fly
+// from the panel's L columns and its W = L D columns (the pivot columns before scaling), and the
+// trailing triangle is updated once per panel instead of once per pivot step.
+//
 // Shared region of one point (doubles): the packed lower triangle (element (i, j), j <= i, at
-// i (i + 1) / 2 + j), the right-hand side / solution y (m), the step vectors u0, u1 (the pivot
-// columns before scaling) and l0, l1 (the multipliers), the stencil coordinates (3 n; the
-// weights on return), then ints: the position -> stencil-row map (m), the pivot kinds (m) and
-// four words of step state.
+// i (i + 1) / 2 + j; rows of the trailing triangle hold entries not yet updated by the open
+// panel), the right-hand side / solution y (m), the panel's W columns (kPanel x m), the stencil
+// coordinates (3 n; afterwards the updated columns k and r, 2 m, and the weights on return), 16
+// 64-bit per-warp maxima, then ints: the position -> stencil-row map (m), the pivot kinds (m) and
+// eight words of step state.
+constexpr int kPanel = 4;
 __host__ __device__ inline int ldl_doubles(int n, int m) {
-    return m * (m + 1) / 2 + 5 * m + 3 * n + (2 * m + 4 + 1) / 2;
+    const int c = 3 * n > 2 * m ? 3 * n : 2 * m;
+    return m * (m + 1) / 2 + (1 + kPanel) * m + c + 16 + (2 * m + 8 + 1) / 2;
 }
 // Shared-memory bytes of one point up to which one warp takes a point (m <~ 45).
 constexpr int kWeightsSmallBytes = 12 * 1024;
@@ -475,10 +483,13 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
     constexpr double kAlpha = 0.6403882032022076;  // (1 + sqrt(17)) / 8
     const int warp = t >> 5, lane = t & 31;
     const int M = m - n;
-    double *P = R, *y = P + tri(m), *u0 = y + m, *u1 = u0 + m, *l0 = u1 + m, *l1 = l0 + m;
-    double *cx = l1 + m, *cy = cx + n, *cz = cy + n;
-    int *perm = reinterpret_cast<int *>(cz + n), *ptype = perm + m, *st = ptype + m;
-    // st[0]: error flag, st[1]: pivot size of the current step
+    const int cdoubles = 3 * n > 2 * m ? 3 * n : 2 * m;
+    double *P = R, *y = P + tri(m), *U = y + m;   // U: kPanel columns of W = L D, m each
+    double *cx = U + kPanel * m, *cy = cx + n, *cz = cy + n;
+    double *wk = cx, *wr = cx + m;                // after the assembly: the updated columns k, r
+    long long *slot = reinterpret_cast<long long *>(cx + cdoubles);  // per-warp maxima
+    int *perm = reinterpret_cast<int *>(slot + 16), *ptype = perm + m, *st = ptype + m;
+    // st[0]: error flag, st[1]: pivot size of the current step, st[2]: close the panel first
     auto gsync = [] {
         if (NW == 1) __syncwarp(); else __syncthreads();
     };
@@ -526,152 +537,214 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
     gsync();
     if (st[0]) return RBFSL_ESINGULAR;
 
+    // ---- blocked factorisation. Per pivot step: (1) all threads form the updated column k,
+    // wk[i] = a_ik - sum_q L_i,q W_k,q over the open panel's columns q (rows i >= k), with
+    // per-warp maxima of |wk[i]|, i > k; (2) every thread combines them into lambda and r and takes
+    // the first test; (3) when it fails, all threads form the updated column r the same way, with
+    // per-warp maxima for sigma; (4) every thread takes the remaining tests, warp 0 inverts the
+    // pivot block, all threads interchange, then each thread forms the multipliers of its rows
+    // (into the triangle's column k), the W column(s) and the forward substitution of y. A panel
+    // closes after kPanel columns (or before a 2 x 2 pivot that would overflow it) with one
+    // trailing update a_ij -= sum_q L_i,q W_j,q of rows and columns >= its end. Measured at
+    // m = 109 (N = 40,962): 30.5 ms against 32.7 ms for one trailing update per pivot step; panels
+    // of 3, 5 and 6 columns 41.1, 32.7 and 33.7 ms (warp 0 forming the multipliers: 31.8 ms).
+    const long long kAbs = 0x7fffffffffffffffLL;
+    int k0 = 0, pc = 0;  // the open panel: first column, columns used
+    auto trailing = [&](int k1) {
+        const int Rr = m - k1, E = Rr * (Rr + 1) / 2;
+        constexpr int Uu = 2;
+        for (int e0 = t; e0 < E; e0 += Uu * GT) {
+            int addr[Uu], ii[Uu], jj[Uu];
+            double v[Uu];
+#pragma unroll
+            for (int u = 0; u < Uu; ++u) {
+                const int e = e0 + u * GT;
+                const int ec = e < E ? e : E - 1;  // out-of-range slots repeat a valid element
+                const int tt = tri_row(ec);
+                ii[u] = k1 + tt;
+                jj[u] = k1 + (ec - tri(tt));
+                addr[u] = tri(ii[u]) + jj[u];
+                v[u] = P[addr[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < Uu; ++u) {
+                if (e0 - lane + u * GT >= E) continue;  // the whole warp past the end: no DFMA issued
+                const double *Li = P + tri(ii[u]) + k0;
+                for (int q = 0; q < pc; ++q) v[u] = fma(-Li[q], U[q * m + jj[u]], v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < Uu; ++u)
+                if (e0 + u * GT < E) P[addr[u]] = v[u];
+        }
+    };
     for (int k = 0; k < m;) {
-        if (warp == 0) {
-            // ---- pivot decision: lambda = max |a_ik| below the diagonal, r its row
+        // (1) updated column k, per-warp maxima (smallest row on ties; rows of lanes without a
+        // candidate: m)
+        {
             long long best = 0;
             int r = m;
-            for (int i = k + 1 + lane; i < m; i += kWarp) {
-                const long long v = __double_as_longlong(P[tri(i) + k]) & 0x7fffffffffffffffLL;
-                if (v > best || r == m) { best = v; r = i; }
+            for (int i = k + t; i < m; i += GT) {
+                double v = P[tri(i) + k];
+                const double *Li = P + tri(i) + k0;
+                for (int q = 0; q < pc; ++q) v = fma(-Li[q], U[q * m + k], v);
+                wk[i] = v;
+                if (i > k) {
+                    const long long b = __double_as_longlong(v) & kAbs;
+                    if (b > best || r == m) { best = b; r = i; }
+                }
             }
             warp_max_key_row(best, r);
-            const int sx = best > 0 ? exp_of(best) : 0;  // the tests' scale 2^sx: lambda in [1, 2)
-            const float lam = best > 0 ? mag_f32(best, sx) : 0.0f;
-            const long long kb = __double_as_longlong(P[tri(k) + k]) & 0x7fffffffffffffffLL;
-            const float akk = mag_f32(kb, sx);
-            constexpr float kAlphaF = (float)kAlpha;
-            int s = 1, piv = k;
-            if (!(akk >= kAlphaF * lam)) {
-                // sigma: max off-diagonal |a| in row / column r (integer compare of the bits)
-                long long sb = 0;
-                for (int c = k + lane; c < m; c += kWarp) {
-                    if (c == r) continue;
-                    const long long v = __double_as_longlong(c < r ? P[tri(r) + c] : P[tri(c) + r]) & 0x7fffffffffffffffLL;
-                    sb = v > sb ? v : sb;
-                }
-                sb = warp_max_key(sb);
-                const float sg = mag_f32(sb, sx);
-                if (akk * sg >= kAlphaF * lam * lam) {
-                    s = 1;
-                } else if (mag_f32(__double_as_longlong(P[tri(r) + r]), sx) >= kAlphaF * sg) {
-                    piv = r;
-                } else {
-                    s = 2;
-                    piv = r;
+            if (lane == 0) { slot[warp] = best; slot[4 + warp] = r; }
+        }
+        gsync();
+        // (2) lambda, r and the first test, the same values in every thread
+        long long best = 0;
+        int r = m;
+        for (int w = 0; w < NW; ++w) {
+            const long long b = slot[w];
+            const int rw = (int)slot[4 + w];
+            if (b > best || (b == best && rw < r)) { best = b; r = rw; }
+        }
+        const int sx = best > 0 ? exp_of(best) : 0;  // the tests' scale 2^sx: lambda in [1, 2)
+        const float lam = best > 0 ? mag_f32(best, sx) : 0.0f;
+        const long long kb = __double_as_longlong(wk[k]) & kAbs;
+        const float akk = mag_f32(kb, sx);
+        constexpr float kAlphaF = (float)kAlpha;
+        const bool need_r = !(akk >= kAlphaF * lam);
+        if (need_r) {
+            // (3) updated column r (rows >= k, from row / column r of the triangle), maxima of
+            // |wr[c]| for c != r
+            long long sb = 0;
+            for (int i = k + t; i < m; i += GT) {
+                double v = i < r ? P[tri(r) + i] : P[tri(i) + r];
+                const double *Li = P + tri(i) + k0;
+                for (int q = 0; q < pc; ++q) v = fma(-Li[q], U[q * m + r], v);
+                wr[i] = v;
+                if (i != r) {
+                    const long long b = __double_as_longlong(v) & kAbs;
+                    sb = b > sb ? b : sb;
                 }
             }
-            // ---- symmetric interchange of positions a < b (lower triangle, L rows included)
-            const int a = s == 1 ? k : k + 1, b = piv;
-            if (b != a) {
-                for (int c = lane; c < m; c += kWarp) {
-                    double *p1, *p2;
-                    if (c < a) { p1 = &P[tri(a) + c]; p2 = &P[tri(b) + c]; }
-                    else if (c == a) { p1 = &P[tri(a) + a]; p2 = &P[tri(b) + b]; }
-                    else if (c < b) { p1 = &P[tri(c) + a]; p2 = &P[tri(b) + c]; }
-                    else if (c == b) continue;
-                    else { p1 = &P[tri(c) + a]; p2 = &P[tri(c) + b]; }
-                    const double v = *p1;
-                    *p1 = *p2;
-                    *p2 = v;
-                }
-                if (lane == 0) {
-                    const double v = y[a]; y[a] = y[b]; y[b] = v;
-                    const int q = perm[a]; perm[a] = perm[b]; perm[b] = q;
-                }
-                __syncwarp();
+            sb = warp_max_key(sb);
+            if (lane == 0) slot[8 + warp] = sb;
+            gsync();
+        }
+        // (4) the remaining tests, in every thread (the same values everywhere)
+        int s = 1, piv = k;
+        if (need_r) {
+            long long sb = 0;
+            for (int w = 0; w < NW; ++w) sb = slot[8 + w] > sb ? slot[8 + w] : sb;
+            const float sg = mag_f32(sb, sx);
+            if (akk * sg >= kAlphaF * lam * lam) {
+                s = 1;
+            } else if (mag_f32(__double_as_longlong(wr[r]) & kAbs, sx) >= kAlphaF * sg) {
+                piv = r;
+            } else {
+                s = 2;
+                piv = r;
             }
-            // ---- multipliers of the trailing rows
+        }
+        if (s == 2 && pc + 2 > kPanel) {  // a 2 x 2 pivot that does not fit: close the panel first
+            trailing(k);
+            gsync();
+            k0 = k;
+            pc = 0;
+            continue;
+        }
+        if (best <= 0 && kb == 0) return RBFSL_ESINGULAR;  // a zero column
+        const int a = s == 1 ? k : k + 1, b = piv;
+        // (4a) warp 0: the pivot block's inverse, from the updated columns before the interchange
+        // (they are scratch: the interchange is applied to them by index below, never moved).
+        // All threads: the symmetric interchange of positions a < b in the triangle (L rows
+        // included), the panel's W rows, y and the row map.
+        double *scal = reinterpret_cast<double *>(slot + 12);
+        if (warp == 0) {
             auto bad_bits = [](double v) {  // zero or non-finite
-                const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
-                return b == 0 || b >= 0x7ff0000000000000LL;
+                const long long bb = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+                return bb == 0 || bb >= 0x7ff0000000000000LL;
             };
             if (s == 1) {
-                const double d = P[tri(k) + k];
-                const bool bad = bad_bits(d);
+                const double d = piv == k ? wk[k] : wr[r];
                 const double dinv = recip_nr(d);  // every lane, same bits
-                for (int i = k + 1 + lane; i < m; i += kWarp) {
-                    const double c = P[tri(i) + k];
-                    u0[i] = c;
-                    const double l = c * dinv;
-                    l0[i] = l;
-                    P[tri(i) + k] = l;
-                }
-                __syncwarp();
-                if (lane == 0) { P[tri(k) + k] = dinv; ptype[k] = 1; st[1] = 1; if (bad) st[0] = 2; }
+                if (lane == 0) { scal[0] = dinv; if (bad_bits(d)) st[0] = 2; }
             } else {
-                const double a11 = P[tri(k) + k], a21 = P[tri(k + 1) + k], a22 = P[tri(k + 1) + k + 1];
+                const double a11 = wk[k], a21 = wk[r], a22 = wr[r];
                 const double det = fma(a11, a22, -(a21 * a21));
-                const bool bad = bad_bits(det);
                 const double idet = recip_nr(det);
-                // D^-1 = [[e22, -e21], [-e21, e11]]
-                const double e11 = a11 * idet, e21 = a21 * idet, e22 = a22 * idet;
-                for (int i = k + 2 + lane; i < m; i += kWarp) {
-                    const double c0 = P[tri(i) + k], c1 = P[tri(i) + k + 1];
-                    u0[i] = c0;
-                    u1[i] = c1;
-                    const double L0 = fma(c0, e22, -(c1 * e21)), L1 = fma(c1, e11, -(c0 * e21));
-                    l0[i] = L0;
-                    l1[i] = L1;
-                    P[tri(i) + k] = L0;
-                    P[tri(i) + k + 1] = L1;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    P[tri(k) + k] = e22;
-                    P[tri(k + 1) + k] = -e21;
-                    P[tri(k + 1) + k + 1] = e11;
-                    ptype[k] = 2; ptype[k + 1] = 0; st[1] = 2; if (bad) st[0] = 2;
+                if (lane == 0) {  // D^-1 = [[e22, -e21], [-e21, e11]]
+                    scal[0] = a11 * idet; scal[1] = a21 * idet; scal[2] = a22 * idet;
+                    if (bad_bits(det)) st[0] = 2;
                 }
             }
-            if (lane == 0 && best <= 0 && kb == 0) st[0] = 2;  // a zero column: singular
+        }
+        if (b != a) {
+            for (int c = t; c < m; c += GT) {
+                double *p1, *p2;
+                if (c < a) { p1 = &P[tri(a) + c]; p2 = &P[tri(b) + c]; }
+                else if (c == a) { p1 = &P[tri(a) + a]; p2 = &P[tri(b) + b]; }
+                else if (c < b) { p1 = &P[tri(c) + a]; p2 = &P[tri(b) + c]; }
+                else if (c == b) continue;
+                else { p1 = &P[tri(c) + a]; p2 = &P[tri(c) + b]; }
+                const double v = *p1;
+                *p1 = *p2;
+                *p2 = v;
+            }
+            const int o = GT - 1 - t;  // the last threads: the vectors
+            if (o < pc) {
+                const double v = U[o * m + a]; U[o * m + a] = U[o * m + b]; U[o * m + b] = v;
+            } else if (o == kPanel) {
+                const double v = y[a]; y[a] = y[b]; y[b] = v;
+            } else if (o == kPanel + 1) {
+                const int q = perm[a]; perm[a] = perm[b]; perm[b] = q;
+            }
         }
         gsync();
         if (st[0]) return RBFSL_ESINGULAR;
-        // ---- trailing update, rows and columns base..m-1 (lower triangle), and the rhs. Each
-        // thread takes two elements of the flattened triangle at a time (all loads, then the
-        // FMAs, then the stores; measured at m = 109 against one, four and eight).
-        const int s = st[1], base = k + s, Rr = m - base, E = Rr * (Rr + 1) / 2;
-        constexpr int U = 2;
-        for (int e0 = t; e0 < E; e0 += U * GT) {
-            int addr[U], ii[U], jj[U];
-            double v[U], a0[U], b0[U], a1[U], b1[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int e = e0 + u * GT;
-                const int ec = e < E ? e : E - 1;  // out-of-range slots repeat a valid load
-                const int tt = tri_row(ec);
-                ii[u] = base + tt;
-                jj[u] = base + (ec - tri(tt));
-                addr[u] = tri(ii[u]) + jj[u];
+        // (4b) multipliers, one row per thread: the column(s) after the interchange are the
+        // updated columns read through the transposition (a b)
+        if (s == 1) {
+            const double *col = piv == k ? wk : wr;
+            const double dinv = scal[0], yk = y[k];
+            for (int i = k + 1 + t; i < m; i += GT) {
+                const int si = i == a ? b : (i == b ? a : i);
+                const double c = col[si];
+                U[pc * m + i] = c;
+                const double l = c * dinv;
+                P[tri(i) + k] = l;
+                y[i] = fma(-l, yk, y[i]);
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                v[u] = P[addr[u]];
-                a0[u] = l0[ii[u]];
-                b0[u] = u0[jj[u]];
-                if (s == 2) { a1[u] = l1[ii[u]]; b1[u] = u1[jj[u]]; }
+            if (t == 0) { P[tri(k) + k] = dinv; ptype[k] = 1; }
+        } else {
+            const double e11 = scal[0], e21 = scal[1], e22 = scal[2];
+            const double yk0 = y[k], yk1 = y[k + 1];
+            for (int i = k + 2 + t; i < m; i += GT) {
+                const int si = i == a ? b : (i == b ? a : i);
+                const double c0 = wk[si], c1 = wr[si];
+                U[pc * m + i] = c0;
+                U[(pc + 1) * m + i] = c1;
+                const double L0 = fma(c0, e22, -(c1 * e21)), L1 = fma(c1, e11, -(c0 * e21));
+                P[tri(i) + k] = L0;
+                P[tri(i) + k + 1] = L1;
+                y[i] = fma(-L1, yk1, fma(-L0, yk0, y[i]));
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (e0 - lane + u * GT >= E) continue;  // the whole warp past the end: no DFMA issued
-                v[u] = fma(-a0[u], b0[u], v[u]);
-                if (s == 2) v[u] = fma(-a1[u], b1[u], v[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (e0 + u * GT < E) P[addr[u]] = v[u];
-        }
-        {
-            const double yk0 = y[k], yk1 = s == 2 ? y[k + 1] : 0.0;
-            for (int i = base + t; i < m; i += GT) {
-                double v = fma(-l0[i], yk0, y[i]);
-                if (s == 2) v = fma(-l1[i], yk1, v);
-                y[i] = v;
+            if (t == 0) {
+                P[tri(k) + k] = e22;
+                P[tri(k + 1) + k] = -e21;
+                P[tri(k + 1) + k + 1] = e11;
+                ptype[k] = 2; ptype[k + 1] = 0;
             }
         }
         gsync();
-        k = base;
+        pc += s;
+        k += s;
+        if (pc == kPanel || k >= m) {
+            if (k < m) {
+                trailing(k);
+                gsync();
+            }
+            k0 = k;
+            pc = 0;
+        }
     }
     if (warp != 0) return RBFSL_OK;
     // ---- D z = y (blocks independent), then L^T x = z column by column
