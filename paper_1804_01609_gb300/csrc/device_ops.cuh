@@ -546,13 +546,13 @@ __device__ __forceinline__ int weights_point_ldl(double *__restrict__ R, const d
     // (into the triangle's column k), the W column(s) and the forward substitution of y. A panel
     // closes after kPanel columns (or before a 2 x 2 pivot that would overflow it) with one
     // trailing update a_ij -= sum_q L_i,q W_j,q of rows and columns >= its end. Measured at
-    // m = 109 (N = 40,962): 30.5 ms against 32.7 ms for one trailing update per pivot step; panels
+    // m = 109 (N = 40,962): 30.3 ms against 32.7 ms for one trailing update per pivot step; panels
     // of 3, 5 and 6 columns 41.1, 32.7 and 33.7 ms (warp 0 forming the multipliers: 31.8 ms).
     const long long kAbs = 0x7fffffffffffffffLL;
     int k0 = 0, pc = 0;  // the open panel: first column, columns used
     auto trailing = [&](int k1) {
         const int Rr = m - k1, E = Rr * (Rr + 1) / 2;
-        constexpr int Uu = 2;
+        constexpr int Uu = 1;  // elements per thread per round (measured: 2 and 4 slower)
         for (int e0 = t; e0 < E; e0 += Uu * GT) {
             int addr[Uu], ii[Uu], jj[Uu];
             double v[Uu];
