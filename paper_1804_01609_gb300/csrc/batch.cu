@@ -94,47 +94,21 @@ __host__ __device__ inline int batch_point_doubles(int mode, int n, int m, int l
     return region > knn ? region : knn;
 }
 
-// Gather-dot of one row from a point's weights (FP64 solution; in mixed precision split into
-// FP32 pairs exactly as a stored pair weight row: wp, formed beforehand by the point's threads,
-// or pair_from here when wp is null), lane t for tracers t, t + 32, ... Members in batches of
-// kGatherRowBatch with all the batch's loads of q issued before its FMAs; the sum runs over j
-// ascending, one fma (pair_fma) per term, as in the single-problem gather kernels.
-constexpr int kGatherRowBatch = 8;
-
-__device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w, const float2 *wp,
-                                             const int32_t *S, int64_t i, int lane) {
-    constexpr int B = kGatherRowBatch;
-    const int in = (int)(b.step & 1), n = b.n, T = b.T;
+// Gather-dot of one row from a point's weights (FP64 solution, split into FP32 pairs in mixed
+// precision as the single-problem path stores them).
+__device__ __forceinline__ void batch_gather(const BatchDesc &b, const double *w, const int32_t *S, int64_t i,
+                                             int lane) {
+    const int in = (int)(b.step & 1);
     if (!b.mixed) {
-        const double *q = (const double *)b.q[in];
-        double *out = (double *)b.q[in ^ 1] + i * T;
-        for (int t = lane; t < T; t += 32) {
-            double acc = 0.0;
-            int j0 = 0;
-            for (; j0 + B <= n; j0 += B) {
-                double qv[B];
-#pragma unroll
-                for (int u = 0; u < B; ++u) qv[u] = q[(int64_t)S[j0 + u] * T + t];
-#pragma unroll
-                for (int u = 0; u < B; ++u) acc = fma(w[j0 + u], qv[u], acc);
-            }
-            for (; j0 < n; ++j0) acc = fma(w[j0], q[(int64_t)S[j0] * T + t], acc);
-            out[t] = acc;
-        }
+        gather_row<double, double>(w, S, b.n, (const double *)b.q[in], b.T, (double *)b.q[in ^ 1] + i * b.T, lane);
     } else {
+        // FP32 pairs: each weight split into a pair exactly as a stored pair weight row, then
+        // the same element arithmetic as gather_dot_pair_kernel
         const float2 *q = (const float2 *)b.q[in];
-        float2 *out = (float2 *)b.q[in ^ 1] + i * T;
-        for (int t = lane; t < T; t += 32) {
+        float2 *out = (float2 *)b.q[in ^ 1] + i * b.T;
+        for (int t = lane; t < b.T; t += 32) {
             float sh = 0.f, sl = 0.f;
-            int j0 = 0;
-            for (; j0 + B <= n; j0 += B) {
-                float2 qv[B];
-#pragma unroll
-                for (int u = 0; u < B; ++u) qv[u] = q[(int64_t)S[j0 + u] * T + t];
-#pragma unroll
-                for (int u = 0; u < B; ++u) pair_fma(wp ? wp[j0 + u] : pair_from(w[j0 + u]), qv[u], sh, sl);
-            }
-            for (; j0 < n; ++j0) pair_fma(wp ? wp[j0] : pair_from(w[j0]), q[(int64_t)S[j0] * T + t], sh, sl);
+            for (int j = 0; j < b.n; ++j) pair_fma(pair_from(w[j]), q[(int64_t)S[j] * b.T + t], sh, sl);
             out[t] = pair_norm(sh, sl);
         }
     }
@@ -179,22 +153,14 @@ __global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__
                 __syncwarp();
                 double *wv = nullptr;
                 rc = weights_point_ldl<1>(A, b.X, S, n, m, b.ell, b.half, px, py, pz, lane, wv);
-                if (rc == RBFSL_OK) {
-                    float2 *wp = nullptr;
-                    if (b.mixed) {  // the pair weights in the (now free) system triangle
-                        wp = reinterpret_cast<float2 *>(A);
-                        for (int j = lane; j < n; j += 32) wp[j] = pair_from(wv[j]);
-                        __syncwarp();
-                    }
-                    batch_gather(b, wv, wp, S, i, lane);
-                }
+                if (rc == RBFSL_OK) batch_gather(b, wv, S, i, lane);
             } else {
                 const int64_t kc = bi[0];
                 const int32_t *Sg = b.Ik + kc * n;
                 double *bb = A, *y = A + m;
                 center_point(b.X, Sg, b.LU + (size_t)kc * m * m, b.perm + (size_t)kc * m, n, m, b.ell, b.half,
                              px, py, pz, bb, y, lane);
-                batch_gather(b, y, nullptr, Sg, i, lane);
+                batch_gather(b, y, Sg, i, lane);
             }
             if (rc != RBFSL_OK) {
                 const int in = (int)(b.step & 1);
@@ -220,19 +186,9 @@ __global__ void __launch_bounds__(128, 4) batch_solve_kernel(const BatchDesc *__
             __syncthreads();
             double *wv = nullptr;
             const int rc = weights_point_ldl<4>(A, b.X, S, n, m, b.ell, b.half, px, py, pz, t, wv);
-            float2 *wp = nullptr;
-            if (b.mixed) {
-                // warp 0's substitutions are done after the barrier and the system triangle is
-                // free: all four warps split the weights into pairs there (wv is set in every
-                // thread; after a failure the values are unused)
-                __syncthreads();
-                wp = reinterpret_cast<float2 *>(A);
-                for (int j = t; j < n; j += 128) wp[j] = pair_from(wv[j]);
-                __syncthreads();
-            }
             if (warp == 0) {
                 if (rc == RBFSL_OK) {
-                    batch_gather(b, wv, wp, S, i, lane);
+                    batch_gather(b, wv, S, i, lane);
                 } else {
                     const int in = (int)(b.step & 1);
                     for (int c = lane; c < b.T; c += 32) {

@@ -885,4 +885,25 @@ __device__ __forceinline__ void center_point(const double *__restrict__ X, const
     else center_point_nu<5>(X, S, Ft, pr, n, m, ell, half, px, py, pz, b, y, lane);
 }
 
+// One output row of the gather-dot for tracer lanes t = lane, lane + 32, ... < T, with the
+// weights w[0..n) and stencil S[0..n) of the row (shared or global memory). FP64:
+// sum_j w_j q[S_j][t]; FP32: difference form q_c + sum_j w_j (q_j - q_c), c = S[0]. The
+// summation runs over j in stencil order (the same order as gather_dot_kernel).
+template <typename R, typename W>
+__device__ __forceinline__ void gather_row(const W *__restrict__ w, const int32_t *__restrict__ S, int n,
+                                           const R *__restrict__ q, int T, R *__restrict__ out, int lane) {
+    for (int t = lane; t < T; t += 32) {
+        R acc = R(0);
+        if (sizeof(R) == 8) {
+            for (int j = 0; j < n; ++j) acc = fma((R)w[j], q[(int64_t)S[j] * T + t], acc);
+            out[t] = acc;
+        } else {
+            const R qc = q[(int64_t)S[0] * T + t];
+            for (int j = 0; j < n; ++j) acc = fma((R)w[j], q[(int64_t)S[j] * T + t] - qc, acc);
+            out[t] = qc + acc;
+        }
+    }
+}
+
+
 }  // namespace rbfsl
