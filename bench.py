@@ -155,7 +155,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one full-size launch of the DIRECT weights kernel, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the kernel version this file ships
 # with; None when no capture of that version exists.
-WEIGHTS_DRAM_BYTES = 15.803648e6 + 1536
+WEIGHTS_DRAM_BYTES = 15.802624e6 + 512
 
 
 def weights_flops(m):
