@@ -133,3 +133,40 @@ def test_served_results_match_oracle(orc):
         strict = r["precision"] == rbfsl.FP64 and r["method"] == rbfsl.LOCAL and r["n"] == 31
         _parity.check_run(f"served[{k}] method={r['method']} N={r['X'].shape[0]} n={r['n']} "
                           f"prec={r['precision']}", g, ref, ex, strict)
+
+
+def test_served_centre_class_mix():
+    """The served workload's shape at small sizes: local centre-stencil requests of all three
+    (n, ell) classes at once (each its own persistent launch on a parallel graph branch), RBF-PU
+    requests on their own streams, 1 to 16 tracers, mixed precision and FP64, staggered arrivals:
+    every request must finish with status 0, no failed point and a finite field."""
+    rng = np.random.default_rng(23)
+    reqs = []
+    classes = [(31, 2, 5), (55, 3, 7), (84, 4, 9)]
+    for k in range(15):
+        N = [642, 2562, 10242][k % 3]
+        T = [1, 7, 16, 3, 11][k % 5]
+        X = inputs.nodes(N, 700 + k)
+        vp = inputs.rigid_rotation_params(inputs.random_unit_vectors(1, rng)[0], 1.0)
+        tr = inputs.config_local_deformation(N=N, n_random=T).tracers
+        q0 = tr(X)[:, :T]
+        if k % 5 == 4:
+            n, ell, p, method, mode = 60, 3, 7, rbfsl.PU, rbfsl.DIRECT
+            C = inputs.fibonacci_nodes(math.ceil(2.5 * N / n))
+        else:
+            (n, ell, p), method, mode, C = classes[k % 3], rbfsl.LOCAL, rbfsl.CENTER, None
+        prec = rbfsl.FP64 if k % 4 == 3 else rbfsl.MIXED
+        reqs.append(dict(X=X, q0=q0, n=n, ell=ell, power=p, vel_kind=0, vel_params=vp, dt=1 / 30,
+                         steps=6 + k % 4, method=method, mode=mode, precision=prec, centers=C))
+    srv = rbfsl.Server(0, budget_bytes=40 * 10 ** 9, max_slots=16)
+    tickets = []
+    for r in reqs:
+        tickets.append(_submit(srv, r))
+        time.sleep(0.002)
+    srv.wait_idle(600)
+    for r, t in zip(reqs, tickets):
+        q, st = srv.result(t, raise_on_failure=False)
+        assert st.status == 0, st.message.decode()
+        assert st.steps == r["steps"] and st.failed_points == 0
+        assert q is not None and np.isfinite(q).all()
+    srv.close()
