@@ -62,8 +62,12 @@ struct WeightsArgs {
 
 // NW warps per point (1 or 4). With NW = 1 a block holds blockDim/32 independent points and
 // the group barrier is __syncwarp; with NW > 1 a block is one point and uses __syncthreads.
+// At most 72 registers (seven 128-thread blocks per SM, no spills): where shared memory allows
+// more than four points per SM (m = 71: 25 KB each) the register file would otherwise cap the
+// blocks at five (11.3 against 10.1 ms at N = 40,962); at m = 109 shared memory caps them at four
+// either way.
 template <int NW, typename WT>
-__global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
+__global__ void __launch_bounds__(NW == 1 ? 128 : NW * 32, 7) weights_kernel(WeightsArgs a, WT *__restrict__ W) {
     extern __shared__ double smem[];
     constexpr int GT = NW * kWarp;
     const int g = threadIdx.x / GT, t = threadIdx.x % GT;
