@@ -137,8 +137,9 @@ int rbfsl_knn_query(const rbfsl_knn_index *index, const double *q, int64_t Nq, i
  * A_jk = phi(|x_Sj - x_Sk|), P_jc = Y_c(x_Sj), Y = real orthonormal spherical harmonics
  * of degree <= ell. Then the interpolant at p_i is sum_j w_ij f_Sj (the system is
  * symmetric). Solved by a symmetric indefinite L D L^T factorisation with Bunch-Kaufman
- * pivoting (1 x 1 and 2 x 2 pivots), one warp per point for small systems, four warps for
- * larger ones; the result does not depend on that choice.
+ * pivoting (1 x 1 and 2 x 2 pivots; blocked: the trailing update once per panel of four pivot
+ * columns), one warp per point for small systems, four warps for larger ones; the result does
+ * not depend on that choice.
  *   x: device N x 3; idx: device Nq x n; p: device Nq x 3; w: device Nq x n of w_dtype
  *   (RBFSL_F64, RBFSL_F32 or RBFSL_F32X2: FP64 solve, result rounded or split into an FP32
  *   pair). status: device Nq or NULL

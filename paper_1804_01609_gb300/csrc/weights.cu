@@ -5,10 +5,11 @@
 // saddle-point system in shared memory (M = (ell+1)^2):
 //     [ A    P ] w~ = [ phi(|p - x_j|) ]      A_jk = |x_j - x_k|^pw   (PHS, zero diagonal)
 //     [ P^T  0 ]      [ Y(p)           ]      P_jc = Y_c(x_j)
-// and solves it by a Bunch-Kaufman L D L^T factorisation (weights_point_ldl): ~m^3 / 3 flops
-// per point, half of Gaussian elimination's, bound by GB300's FP64 rate. Small systems take one
-// warp per point (four points per block); larger ones four warps per point, several
-// points per SM so that one point's pivot decisions overlap the others' updates.
+// and solves it by a blocked Bunch-Kaufman L D L^T factorisation (weights_point_ldl: panels of
+// four pivot columns updated on the fly, one trailing update per panel): ~m^3 / 3 flops per
+// point, half of Gaussian elimination's, bound by GB300's FP64 rate. Small systems take one warp
+// per point (four points per block); larger ones four warps per point, several points per SM so
+// that one point's pivot steps overlap the others' trailing updates.
 #include "common.cuh"
 #include "kernels.cuh"
 #include "device_ops.cuh"
