@@ -109,6 +109,24 @@ def test_pu_every_point_covered(orc):
     assert np.isfinite(pu.apply(P, np.ones(len(X)))).all()
 
 
+
+@pytest.mark.parametrize("n", [31, 49, 84])
+def test_pu_patch_covering_depends_on_the_overlap(orc, n):
+    """Eqs. rad_patches and num_patches fix R = 2 sqrt(n / N) and M = ceil(a N / n) patches; the
+    patches must cover the sphere (Sec. 2.3). With Fibonacci centres at N = 40,962 an overlap
+    a = 2.5 covers a dense sample of the sphere, while a = 1.5 leaves points whose nearest centre
+    is farther than R (the bench's (n, a) sweep reports those departure points as uncovered)."""
+    N = 40962
+    R = 2.0 * math.sqrt(n / N)
+    P = inputs.random_unit_vectors(20000, np.random.default_rng(29))
+    gap = {}
+    for a in (1.5, 2.5):
+        C = inputs.fibonacci_nodes(math.ceil(a * N / n))
+        idx = orc.knn(C, P, 1)[:, 0]
+        gap[a] = np.linalg.norm(P - C[idx], axis=1).max() / R
+    assert gap[2.5] < 1.0 < gap[1.5]
+
+
 def test_oracle_global_iteration_diverges_at_the_workloads_eps_h(orc):
     """Gaussian eps = 3 on 2,562 nodes has the eps h of the global workload (eps = 6 on 10,242):
     the interpolation matrix is numerically singular (smallest LU pivot ~1e-14), and the FP64
