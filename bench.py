@@ -1141,7 +1141,7 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 Bunch-Kaufman LDL^T, m = 109)",
+        "roofline": {"bound": "alu", "kernel": "weights_kernel<4, float2> (FP64 blocked Bunch-Kaufman LDL^T, m = 109)",
                      "achieved": w_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": w_tflops / fp64_peak, "traffic": WEIGHTS_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read + _write of this kernel version, "
